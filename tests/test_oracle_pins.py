@@ -1,0 +1,399 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks an oracle routine against something other than itself:
+exhaustive search, a closed form, a textbook special case, an invariant or a
+duality bound.  Marked "not gpu" (no marker): runs on CPU.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.helpers import feasible_local, random_laminar
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 / Proposition 1
+# ---------------------------------------------------------------------------
+
+def test_hierarchical_definition():
+    # Sec. 2.1, Definition 1
+    assert oracle.is_hierarchical([0b0011, 0b1100, 0b1111])
+    assert oracle.is_hierarchical([0b0011, 0b0011])
+    assert not oracle.is_hierarchical([0b0011, 0b0110])
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_greedy_is_optimal_vs_brute_force(seed):
+    """Proposition 1: Algorithm 1 solves Eq. (11)-(13) optimally (exchange argument);
+    checked by exhaustive 2^M search on random hierarchical families."""
+    rng = np.random.default_rng(seed)
+    M = int(rng.integers(1, 13))
+    S, C = random_laminar(M, rng)
+    assert oracle.is_hierarchical(S)
+    for _ in range(20):
+        pt = rng.normal(size=M)
+        if rng.random() < 0.3:  # ties
+            pt = np.round(pt, 1)
+        x = oracle.greedy(pt, S, C)
+        mask = sum(1 << j for j in range(M) if x[j])
+        assert feasible_local(mask, S, C)
+        assert np.all(pt[x == 1] > 0)
+        best, _ = oracle.brute_force(pt, S, C)
+        assert float(pt @ x) == pytest.approx(best, abs=1e-12)
+
+
+def _walk_greedy(pt, S, C):
+    """Second, independent form of the greedy: visit items by non-increasing p~
+    (ties: lower index) and accept an item if p~ > 0 and every set containing it
+    still has room.  Equivalent to Algorithm 1's bottom-up pass for laminar sets."""
+    M = len(pt)
+    order = sorted(range(M), key=lambda j: (-pt[j], j))
+    cnt = [0] * len(S)
+    x = [0] * M
+    for j in order:
+        if pt[j] <= 0:
+            continue
+        if all(cnt[l] < C[l] for l in range(len(S)) if (S[l] >> j) & 1):
+            x[j] = 1
+            for l in range(len(S)):
+                if (S[l] >> j) & 1:
+                    cnt[l] += 1
+    return np.array(x)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_greedy_two_forms_agree(seed):
+    rng = np.random.default_rng(100 + seed)
+    M = int(rng.integers(1, 20))
+    S, C = random_laminar(M, rng, max_nodes=8)
+    for _ in range(30):
+        pt = np.round(rng.normal(size=M), 1)  # many exact ties
+        assert np.array_equal(oracle.greedy(pt, S, C), _walk_greedy(pt, S, C))
+
+
+def test_greedy_sort_direction_and_caps():
+    """Algorithm 1 keeps the LARGEST cost-adjusted profits (reading R1) and counts
+    items against C_l (reading R2)."""
+    pt = np.array([0.1, 0.5, 0.3, -0.2, 0.4])
+    S = [0b00111, 0b11111]  # {0,1,2} cap 1, all cap 2
+    C = [1, 2]
+    x = oracle.greedy(pt, S, C)
+    # group {0,1,2}: keep item 1 (0.5); overall cap 2: items 1 and 4 (0.4)
+    assert x.tolist() == [0, 1, 0, 0, 1]
+
+
+def test_reduced_costs_closed_form():
+    p = np.array([1.0, 2.0])
+    b = np.array([[0.5, 0.25], [1.0, 0.0]])
+    lam = np.array([2.0, 4.0])
+    assert oracle.reduced_costs(p, b, lam).tolist() == [1.0 - 1.0 - 1.0, 2.0 - 2.0]
+
+
+# ---------------------------------------------------------------------------
+# Algorithms 3-4 Map: the per-user step function of k-consumption in lambda_k
+# ---------------------------------------------------------------------------
+
+def _consumption_bf(p_i, b_i, S, C, lam, k, lk):
+    lam2 = lam.copy()
+    lam2[k] = lk
+    pt = p_i - b_i @ lam2
+    _, x = oracle.brute_force(pt, S, C)
+    return float(b_i[:, k] @ x)
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_scd_map_is_the_consumption_step_function(seed):
+    """The pairs emitted by the Map of Algorithm 4 describe the user's k-consumption as
+    lambda_k varies with the other multipliers fixed: at any generic lambda_k,
+    consumption = sum of v2 over emitted v1 > lambda_k (reading R4).  The consumption
+    is computed here by exhaustive search, independent of Algorithm 1."""
+    rng = np.random.default_rng(200 + seed)
+    M = int(rng.integers(1, 8))
+    K = int(rng.integers(1, 4))
+    S, C = random_laminar(M, rng)
+    p_i = rng.uniform(0, 1, size=M)
+    b_i = rng.uniform(0, 1, size=(M, K)) * (rng.random((M, K)) < 0.7)
+    lam = rng.uniform(0, 0.8, size=K)
+    ek, v1, v2 = oracle.scd_map_user(p_i, b_i, S, C, lam)
+    assert np.all(v2 > 0)          # consumption never decreases as lambda_k decreases
+    assert np.all(v1 > 0)
+    for k in range(K):
+        sel = ek == k
+        for lk in rng.uniform(0, 3.0, size=25):
+            if sel.any() and np.min(np.abs(v1[sel] - lk)) < 1e-9:
+                continue
+            want = _consumption_bf(p_i, b_i, S, C, lam, k, lk)
+            got = float(v2[sel & (v1 > lk)].sum())
+            assert got == pytest.approx(want, abs=1e-9)
+        # at lambda_k -> infinity the user consumes nothing of k
+        assert _consumption_bf(p_i, b_i, S, C, lam, k, 1e9) == 0.0
+
+
+def test_scd_map_single_item_closed_form():
+    """One item, one knapsack, no local constraint: the only breakpoint is the zero
+    crossing p/b, with jump b (Algorithm 3's zero-crossing candidate)."""
+    ek, v1, v2 = oracle.scd_map_user([0.6], [[0.3]], [], [], [0.0])
+    assert ek.tolist() == [0] and v1 == pytest.approx([2.0]) and v2 == pytest.approx([0.3])
+
+
+def test_scd_map_two_items_cap_one_hand_example():
+    """Two items sharing one knapsack under a cap of 1 (MCKP-like user).
+    z_0 = 1 - 0.5 l, z_1 = 0.8 - 0.1 l.  Zero crossings: 2 and 8; crossing:
+    (1-0.8)/(0.5-0.1) = 0.5.  For l > 8 nothing; 0.5 < l < 8: item 1 (0.1);
+    l < 0.5: item 0 (0.5).  Emissions: (8, 0.1), (0.5, 0.4)."""
+    ek, v1, v2 = oracle.scd_map_user([1.0, 0.8], [[0.5], [0.1]], [0b11], [1], [0.0])
+    assert v1.tolist() == pytest.approx([8.0, 0.5])
+    assert v2.tolist() == pytest.approx([0.1, 0.4])
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 4 Reduce (reading R6)
+# ---------------------------------------------------------------------------
+
+def _reduce_bf(v1, v2, B):
+    cands = sorted(set([0.0] + list(v1)))
+    for v in cands:  # smallest first
+        if sum(m for a, m in zip(v1, v2) if a > v) <= B:
+            return v
+    raise AssertionError
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_scd_reduce_matches_definition(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(0, 40))
+    v1 = np.round(rng.uniform(0.01, 2, size=n), 2)   # repeated values
+    v2 = rng.uniform(0.01, 1, size=n)
+    B = float(rng.uniform(0, max(v2.sum(), 0.1) * 1.2))
+    assert oracle.scd_reduce(v1, v2, B) == _reduce_bf(list(v1), list(v2), B)
+
+
+def test_dantzig_critical_ratio_K1_M1():
+    """Sec. 4.4: for K=1 SCD is the rounded fractional knapsack.  With M=1, L=0 the
+    threshold equals Dantzig's critical ratio: sort users by p/b decreasingly and
+    stop at the first whose b no longer fits in B."""
+    rng = np.random.default_rng(7)
+    N = 500
+    p = rng.uniform(0, 1, size=(N, 1))
+    b = rng.uniform(0.05, 1, size=(N, 1, 1))
+    B = np.array([0.3 * b.sum()])
+    lam1, _, _ = oracle.scd_step(p, b, [], [], np.zeros(1), B)
+    ratio = p[:, 0] / b[:, 0, 0]
+    order = np.argsort(-ratio, kind="stable")
+    cum = np.cumsum(b[order, 0, 0])
+    crit = order[np.argmax(cum > B[0])]
+    assert lam1[0] == pytest.approx(ratio[crit], rel=1e-14)
+    # the critical user is tied at the threshold itself; just above it the
+    # consumption fits (Eq. (9)) and just below it does not
+    _, R_hi, _, _ = oracle.user_pass(p, b, [], [], lam1 * (1 + 1e-9))
+    _, R_lo, _, _ = oracle.user_pass(p, b, [], [], lam1 * (1 - 1e-9))
+    assert R_hi[0] <= B[0] < R_lo[0]
+
+
+def test_scd_K1_fixed_point_after_one_step():
+    """Sec. 4.4: for K=1 the Map does not depend on lambda^t, so one SCD step from any
+    start reaches the same lambda, which is then a fixed point (cf. Table 1, M=1)."""
+    rng = np.random.default_rng(8)
+    N, M = 300, 4
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, 1))
+    S, C = [0b0011, 0b1111], [1, 2]
+    B = np.array([0.2 * b.sum()])
+    l1a, _, _ = oracle.scd_step(p, b, S, C, np.zeros(1), B)
+    l1b, _, _ = oracle.scd_step(p, b, S, C, np.array([0.77]), B)
+    l2, _, _ = oracle.scd_step(p, b, S, C, l1a, B)
+    assert l1a[0] == l1b[0] == l2[0]
+
+
+# ---------------------------------------------------------------------------
+# Eq. (14), duality, Everett's property, LP bound, Danskin gradient, Sec. 5.4
+# ---------------------------------------------------------------------------
+
+def test_dd_update_closed_form():
+    lam = np.array([0.5, 0.1, 0.0])
+    R = np.array([10.0, 2.0, 1.0])
+    B = np.array([8.0, 4.0, 3.0])
+    out = oracle.dd_update(lam, R, B, 0.1)
+    assert out.tolist() == pytest.approx([0.7, 0.0, 0.0])
+
+
+def _tiny_instance(seed, N=3, M=3, K=2):
+    rng = np.random.default_rng(seed)
+    S, C = random_laminar(M, rng, max_nodes=3)
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, K))
+    B = 0.3 * b.sum(axis=(0, 1))
+    return p, b, S, C, B
+
+
+def _all_feasible_primal(p, b, S, C, B, Bcap=None):
+    """Exhaustive maximum of Eq. (1) subject to (2)-(4); Bcap overrides B per k
+    (np.inf = unconstrained)."""
+    N, M, K = b.shape
+    Bc = B if Bcap is None else Bcap
+    local = [m for m in range(1 << M) if feasible_local(m, S, C)]
+    best = -1.0
+    for combo in itertools.product(local, repeat=N):
+        x = np.array([[(m >> j) & 1 for j in range(M)] for m in combo], dtype=float)
+        R = np.einsum("ij,ijk->k", x, b)
+        if np.all(R <= Bc + 1e-12):
+            best = max(best, float((p * x).sum()))
+    return best
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_weak_duality(seed):
+    """Eq. (5)-(10): g(lambda) >= every feasible primal value, for every lambda >= 0."""
+    p, b, S, C, B = _tiny_instance(400 + seed)
+    best = _all_feasible_primal(p, b, S, C, B)
+    rng = np.random.default_rng(seed)
+    for _ in range(30):
+        lam = rng.uniform(0, 2, size=B.shape)
+        assert oracle.dual_value(p, b, S, C, lam, B) >= best - 1e-12
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_everett_property(seed):
+    """Sec. 4.4 (Everett / Shapiro): x(lambda) is optimal for the KP whose budgets are
+    replaced by its own consumption R_k(lambda) where lambda_k > 0 (and left free where
+    lambda_k = 0)."""
+    p, b, S, C, B = _tiny_instance(500 + seed)
+    rng = np.random.default_rng(seed)
+    for _ in range(4):
+        lam = rng.uniform(0, 1.5, size=B.shape) * (rng.random(B.shape) < 0.8)
+        x, R, _, primal = oracle.user_pass(p, b, S, C, lam)
+        cap = np.where(lam > 0, R, np.inf)
+        assert primal == pytest.approx(_all_feasible_primal(p, b, S, C, B, cap), abs=1e-12)
+
+
+def test_lagrangian_dual_equals_lp_relaxation():
+    """The Lagrangian dual min_lambda g(lambda) of a KP whose local constraints form a
+    laminar (matroid) family equals its LP relaxation (the local polytope is integral).
+    g evaluated at the LP's optimal multipliers of the global rows must equal the LP
+    optimum; any other lambda gives more (weak duality)."""
+    linprog = pytest.importorskip("scipy.optimize").linprog
+    rng = np.random.default_rng(11)
+    N, M, K = 30, 4, 2
+    S, C = [0b0011, 0b1111], [1, 2]
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, K))
+    B = 0.15 * b.sum(axis=(0, 1))
+    nv = N * M
+    A_glob = b.reshape(nv, K).T
+    rows = [A_glob]
+    rhs = [B]
+    for i in range(N):
+        for s, c in zip(S, C):
+            r = np.zeros(nv)
+            for j in range(M):
+                if (s >> j) & 1:
+                    r[i * M + j] = 1
+            rows.append(r[None, :])
+            rhs.append(np.array([c]))
+    res = linprog(-p.reshape(-1), A_ub=np.vstack(rows), b_ub=np.concatenate(rhs),
+                  bounds=[(0, 1)] * nv, method="highs")
+    assert res.status == 0
+    lp = -res.fun
+    lam_star = -res.ineqlin.marginals[:K]
+    g = oracle.dual_value(p, b, S, C, lam_star, B)
+    assert g == pytest.approx(lp, rel=1e-9)
+    for _ in range(20):
+        lam = np.maximum(lam_star + rng.normal(scale=0.05, size=K), 0)
+        assert oracle.dual_value(p, b, S, C, lam, B) >= lp - 1e-9
+
+
+def test_danskin_gradient_by_central_differences():
+    """At a generic lambda the maximiser x* is unique and locally constant, so
+    dg/dlambda_k = B_k - R_k, dg/dp_ij = x*_ij and dg/dB_k = lambda_k."""
+    rng = np.random.default_rng(12)
+    N, M, K = 50, 5, 3
+    S, C = [0b00111, 0b11111], [1, 2]
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, K))
+    B = 0.2 * b.sum(axis=(0, 1))
+    lam = rng.uniform(0.05, 0.4, size=K)
+    x, R, _, _ = oracle.user_pass(p, b, S, C, lam)
+    h = 1e-7
+    for k in range(K):
+        e = np.zeros(K)
+        e[k] = h
+        fd = (oracle.dual_value(p, b, S, C, lam + e, B) -
+              oracle.dual_value(p, b, S, C, lam - e, B)) / (2 * h)
+        assert fd == pytest.approx(B[k] - R[k], rel=1e-6, abs=1e-6)
+        e2 = np.zeros(K)
+        e2[k] = h
+        fdB = (oracle.dual_value(p, b, S, C, lam, B + e2) -
+               oracle.dual_value(p, b, S, C, lam, B - e2)) / (2 * h)
+        assert fdB == pytest.approx(lam[k], rel=1e-6)
+    for (i, j) in [(0, 0), (3, 2), (7, 4), (11, 1)]:
+        pp = p.copy()
+        pp[i, j] += h
+        pm = p.copy()
+        pm[i, j] -= h
+        fd = (oracle.dual_value(pp, b, S, C, lam, B) - oracle.dual_value(pm, b, S, C, lam, B)) / (2 * h)
+        assert fd == pytest.approx(float(x[i, j]), abs=1e-6)
+
+
+def test_mckp_special_case():
+    """Sec. 2.2: K=1, one set with C=1 is the multiple-choice KP; the per-user
+    subproblem then picks the single item of largest positive p~."""
+    rng = np.random.default_rng(13)
+    N, M = 40, 6
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, 1))
+    lam = np.array([0.7])
+    x, _, _, _ = oracle.user_pass(p, b, [(1 << M) - 1], [1], lam)
+    pt = p - 0.7 * b[:, :, 0]
+    for i in range(N):
+        j = int(np.argmax(pt[i]))
+        want = np.zeros(M, dtype=int)
+        if pt[i, j] > 0:
+            want[j] = 1
+        assert x[i].tolist() == want.tolist()
+
+
+def test_postprocess_feasible_and_ordered():
+    """Sec. 5.4: users are reset in non-decreasing order of the cost-adjusted group
+    profit until every global constraint holds."""
+    rng = np.random.default_rng(14)
+    N, M, K = 200, 4, 3
+    S, C = [0b1111], [2]
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, K))
+    B = 0.05 * b.sum(axis=(0, 1))
+    lam = np.zeros(K)
+    x, R, _, _ = oracle.user_pass(p, b, S, C, lam)
+    assert np.any(R > B)
+    x2, nreset = oracle.postprocess(p, b, lam, B, x)
+    R2 = np.einsum("ij,ijk->k", x2, b)
+    assert np.all(R2 <= B + 1e-12)
+    gp = (p * x).sum(1) - np.einsum("ij,ijk,k->i", x, b, lam)
+    order = np.lexsort((np.arange(N), gp))
+    reset_users = order[:nreset]
+    assert np.all(x2[reset_users] == 0)
+    keep = order[nreset:]
+    assert np.array_equal(x2[keep], x[keep])
+    # minimal: un-resetting the last reset user breaks feasibility
+    last = order[nreset - 1]
+    R3 = R2 + np.einsum("j,jk->k", x[last], b[last])
+    assert np.any(R3 > B)
+
+
+def test_scd_emitted_mass_is_consumption_at_zero():
+    """Summing a user's emitted v2 for k over all v1 > 0 gives the user's
+    k-consumption just above lambda_k = 0 (others fixed)."""
+    rng = np.random.default_rng(15)
+    N, M, K = 40, 5, 3
+    S, C = [0b00011, 0b11100, 0b11111], [1, 2, 2]
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, K))
+    B = 0.2 * b.sum(axis=(0, 1))
+    lam = rng.uniform(0, 0.5, size=K)
+    _, _, mass = oracle.scd_step(p, b, S, C, lam, B)
+    for k in range(K):
+        lam0 = lam.copy()
+        lam0[k] = 1e-12
+        _, R0, _, _ = oracle.user_pass(p, b, S, C, lam0)
+        assert mass[k] == pytest.approx(R0[k], rel=1e-12)
