@@ -1,0 +1,193 @@
+/*
+ * kp.h -- C ABI of the GB300 dual-decomposition knapsack library
+ * (method of Zhang, Qi, Hua, Yang, "Solving Billion-Scale Knapsack Problems",
+ * WWW 2020, arXiv 2002.00352).
+ *
+ * Problem (Sec. 2, Eq. (1)-(4)): N users ("groups"), M items per user, K
+ * global knapsacks, L local count constraints shared by all users:
+ *
+ *     max  sum_ij p_ij x_ij
+ *     s.t. sum_ij b_ijk x_ij <= B_k            for every knapsack k
+ *          sum_{j in S_l} x_ij <= C_l          for every user i and set l
+ *          x_ij in {0, 1}
+ *
+ * with p, b >= 0 and B, C > 0.  The local sets must be hierarchical
+ * (Sec. 2.1, Definition 1: any two are disjoint or nested); the per-user
+ * subproblem at fixed multipliers (Eq. (11)-(13)) is then solved exactly by
+ * the greedy of Algorithm 1.
+ *
+ * Conventions shared by every call:
+ *   - "device" pointers are CUDA global memory of the current device; the
+ *     caller owns all of them.  kp_create borrows the instance arrays: they
+ *     must stay allocated and unchanged (except B, see below) until
+ *     kp_destroy.  The handle owns only its scratch memory.
+ *   - Every compute call is asynchronous on the given stream (a
+ *     cudaStream_t passed as void*; NULL = legacy default stream).  Outputs
+ *     are valid after the stream has been synchronised.
+ *   - Multipliers lambda are FP64 [K] device arrays with lambda_k >= 0
+ *     (Eq. (10)).  Kernels round lambda to FP32 once per call; reduced costs
+ *     and breakpoints are computed in FP32, all sums over users in FP64 or
+ *     exact 64-bit fixed point.
+ *   - Calls on one handle must be ordered on one stream (they share the
+ *     handle's scratch).
+ *   - Return value: KP_OK, or an error code with nothing written to any
+ *     output; kp_last_error() then describes the error (thread-local).
+ *     Errors detected by a kernel (a bounded wait that ran out, a selection
+ *     that did not converge) are reported by kp_device_status().
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef KP_H
+#define KP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KP_OK = 0,
+    KP_EINVAL = 1,   /* invalid argument or instance (sizes, tree, caps) */
+    KP_ENOMEM = 2,   /* device allocation failed */
+    KP_ECUDA = 3,    /* a CUDA runtime call failed */
+    KP_ETIMEOUT = 4, /* a kernel's bounded wait ran out (device status) */
+    KP_ESTATE = 5,   /* inconsistent state, e.g. threshold search did not converge */
+    KP_EDATA = 6     /* instance data violate Sec. 2 (negative or non-finite p, b;
+                        B <= 0; malformed CSR) */
+} kp_status;
+
+enum { KP_B_DENSE = 0, KP_B_CSR = 1 };
+
+/* limits of this implementation */
+enum { KP_MAX_M = 64, KP_MAX_L = 16, KP_MAX_K = 2048 };
+
+typedef struct kp_problem kp_problem;
+
+/* Instance description (Sec. 2, Eq. (1)-(4)).
+ *
+ *   N, M, K      users, items per user (1..KP_MAX_M), knapsacks (1..KP_MAX_K)
+ *   p            device float32 [N*M], p_ij at i*M+j, >= 0
+ *   b_layout     KP_B_DENSE or KP_B_CSR
+ *   b_dense      device float32 [N*M*K], b_ijk at (i*M+j)*K+k, >= 0
+ *   csr_user_off device int64 [N+1]: entries of user i are
+ *                [csr_user_off[i], csr_user_off[i+1]) of csr_val / csr_k
+ *   csr_item_nnz device uint8 [N*M]: the entries of user i are grouped by
+ *                item in item order; item j owns csr_item_nnz[i*M+j] of them
+ *   csr_val      device float32 [nnz] b_ijk of the entry, >= 0
+ *   csr_k        device int16 [nnz] k of the entry, 0 <= k < K, strictly
+ *                increasing within an item
+ *   B            device float64 [K], B_k > 0.  Read at every call, so the
+ *                caller may change the budgets between calls (e.g. an outer
+ *                gradient loop on B).
+ *   L            number of local constraints (0..KP_MAX_L)
+ *   S            host uint64 [L]: bit j of S[l] set iff item j is in S_l
+ *   C            host int32 [L]: caps C_l >= 1 (Eq. (3))
+ *   S and C are copied at kp_create.
+ */
+typedef struct {
+    int64_t N;
+    int32_t M;
+    int32_t K;
+    const float *p;
+    int32_t b_layout;
+    const float *b_dense;
+    const int64_t *csr_user_off;
+    const uint8_t *csr_item_nnz;
+    const float *csr_val;
+    const int16_t *csr_k;
+    const double *B;
+    int32_t L;
+    const uint64_t *S;
+    const int32_t *C;
+} kp_desc;
+
+/* Validates the description (sizes, hierarchical sets per Sec. 2.1, caps),
+ * scans the instance once on the device (p, b finite and >= 0; CSR offsets
+ * consistent with item counts, k in range and increasing per item; B > 0),
+ * allocates the scratch and returns a handle in *out.  Synchronous.
+ * KP_EINVAL / KP_EDATA / KP_ENOMEM / KP_ECUDA on failure (*out untouched). */
+kp_status kp_create(const kp_desc *desc, kp_problem **out);
+
+/* Frees the handle's scratch.  Synchronises the device.  NULL is a no-op. */
+kp_status kp_destroy(kp_problem *h);
+
+/* Per-user decisions at lambda: Algorithm 1 for every user (Sec. 4.2).
+ * x_bits: device uint32 [N*W], W = ceil(M/32); bit (j%32) of word
+ * i*W + j/32 is x_ij. */
+kp_status kp_solve_users(kp_problem *h, const double *lambda, uint32_t *x_bits, void *stream);
+
+/* Map + Reduce of Algorithm 2 at lambda: R_k = sum_i sum_j b_ijk x_ij
+ * (device float64 [K]), dual_sum = sum_ij p~_ij x_ij, primal_sum =
+ * sum_ij p_ij x_ij and g = dual_sum + sum_k lambda_k B_k (the dual
+ * objective, Eq. (5)) (device float64 scalars).  x_bits as in
+ * kp_solve_users; every output pointer may be NULL. */
+kp_status kp_reduce_consumption(kp_problem *h, const double *lambda, double *R,
+                                double *dual_sum, double *primal_sum, double *g,
+                                uint32_t *x_bits, void *stream);
+
+/* Dual objective (Eq. (5)): g(lambda) = sum_i max_x sum_j p~_ij x_ij + sum_k lambda_k B_k,
+ * written to the device float64 scalar g. */
+kp_status kp_dual_value(kp_problem *h, const double *lambda, double *g, void *stream);
+
+/* One dual-descent iteration (Eq. (14), Algorithm 2):
+ * lambda_next_k = max(lambda_k + alpha (R_k - B_k), 0).  lambda_next may
+ * alias lambda.  R (device [K]) may be NULL. */
+kp_status kp_dd_step(kp_problem *h, const double *lambda, double alpha, double *lambda_next,
+                     double *R, void *stream);
+
+/* Map of Algorithm 4 (with the candidate sets of Algorithm 3) at lambda:
+ * every user's breakpoints of its k-consumption in lambda_k (others fixed)
+ * are aggregated into the handle's per-knapsack histograms (Sec. 5.2's
+ * bucketing, centred at lambda_k).  The state at lambda is reduced in the
+ * same pass into the optional outputs (as in kp_reduce_consumption).
+ * Must be followed by kp_threshold_select with the same lambda. */
+kp_status kp_scd_breakpoints(kp_problem *h, const double *lambda, double *R, double *dual_sum,
+                             double *primal_sum, uint32_t *x_bits, void *stream);
+
+/* Reduce of Algorithm 4 for every k:
+ *   lambda_next_k = min { v in {0} U {breakpoints} : sum_{v1 > v} v2 <= B_k }
+ * found exactly among the FP32 breakpoints (histogram, then a buffered
+ * exact selection; when the crossing lies outside the buffered window the
+ * user pass is re-run to narrow it, up to a fixed number of rounds, all on
+ * the device).  lambda must be the one given to kp_scd_breakpoints.
+ * lambda_next must not alias lambda. */
+kp_status kp_threshold_select(kp_problem *h, const double *lambda, double *lambda_next, void *stream);
+
+/* One full iteration of Algorithm 4: kp_scd_breakpoints + kp_threshold_select. */
+kp_status kp_scd_step(kp_problem *h, const double *lambda, double *lambda_next, double *R,
+                      double *dual_sum, double *primal_sum, void *stream);
+
+/* Gradient of the dual g(lambda, p, B) of Eq. (5) by Danskin's theorem at the
+ * maximiser x* (from kp_solve_users / kp_reduce_consumption at the same
+ * lambda), each scaled by the device float64 scalar *upstream:
+ *   grad_lambda_k = upstream (B_k - R_k)       (R from the same lambda)
+ *   grad_p_ij     = upstream x*_ij             (device float32 [N*M])
+ *   grad_B_k      = upstream lambda_k
+ * Any of the three outputs may be NULL.  (The paper gives no gradient; this
+ * is the derivative of its dual function, Eq. (5).) */
+kp_status kp_dual_backward(kp_problem *h, const double *lambda, const uint32_t *x_bits,
+                           const double *R, const double *upstream, double *grad_lambda,
+                           float *grad_p, double *grad_B, void *stream);
+
+/* Synchronises the stream and returns the device-side status accumulated by
+ * the handle's kernels since the last call (KP_OK, KP_ETIMEOUT or
+ * KP_ESTATE), then clears it. */
+kp_status kp_device_status(kp_problem *h, void *stream);
+
+/* Counters of the last kp_threshold_select on this handle (device values,
+ * copied synchronously): out[0] = user passes run for the selection
+ * (1 = resolved from the buffered window), out[1] = knapsacks resolved
+ * from the histogram alone (lambda = 0), out[2] = buffer overflows. */
+kp_status kp_select_stats(kp_problem *h, int64_t out[3], void *stream);
+
+/* Thread-local description of the last error on this thread. */
+const char *kp_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int kp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KP_H */

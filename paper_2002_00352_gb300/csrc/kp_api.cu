@@ -1,0 +1,354 @@
+// kp_api.cu -- the extern "C" entry points declared in include/kp.h.
+//
+// Host-side validation of the instance description, creation of the
+// handle's scratch memory, and the ordering of the kernel launches that make
+// up one call.  No exception crosses the interface; errors are returned as
+// kp_status with a thread-local message.
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kp_internal.h"
+
+namespace kp {
+int pass_grid_size(const Params &P);
+}
+
+struct kp_problem {
+    kp::Params P;
+    kp::Scratch S;
+    int device;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+kp_status fail(kp_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+kp_status cuda_fail(cudaError_t e, const char *where) {
+    return fail(e == cudaErrorMemoryAllocation ? KP_ENOMEM : KP_ECUDA, "%s: %s", where,
+                cudaGetErrorString(e));
+}
+
+#define KP_CUDA(call, where)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+template <class T>
+kp_status alloc(kp_problem *h, T **out, size_t count, const char *what) {
+    void *p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(KP_ENOMEM, "cudaMalloc(%zu bytes) for %s: %s", bytes, what,
+                                      cudaGetErrorString(e));
+    h->allocs.push_back(p);
+    e = cudaMemset(p, 0, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+    *out = (T *)p;
+    return KP_OK;
+}
+
+void free_all(kp_problem *h) {
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+bool check_handle(kp_problem *h) { return h != nullptr && h->P.N > 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *kp_last_error(void) { return g_err; }
+
+int kp_version(void) { return 100; }
+
+kp_status kp_create(const kp_desc *d, kp_problem **out) {
+    g_err[0] = 0;
+    if (!d || !out) return fail(KP_EINVAL, "kp_create: NULL argument");
+    if (d->N < 1) return fail(KP_EINVAL, "N must be >= 1 (got %lld)", (long long)d->N);
+    if (d->M < 1 || d->M > KP_MAX_M) return fail(KP_EINVAL, "M must be in 1..%d (got %d)", KP_MAX_M, d->M);
+    if (d->K < 1 || d->K > KP_MAX_K) return fail(KP_EINVAL, "K must be in 1..%d (got %d)", KP_MAX_K, d->K);
+    if (d->L < 0 || d->L > KP_MAX_L) return fail(KP_EINVAL, "L must be in 0..%d (got %d)", KP_MAX_L, d->L);
+    if (!d->p || !d->B) return fail(KP_EINVAL, "p and B must be device pointers");
+    if (d->b_layout == KP_B_DENSE) {
+        if (!d->b_dense) return fail(KP_EINVAL, "dense layout needs b_dense");
+    } else if (d->b_layout == KP_B_CSR) {
+        if (!d->csr_user_off || !d->csr_item_nnz || !d->csr_val || !d->csr_k)
+            return fail(KP_EINVAL, "CSR layout needs csr_user_off, csr_item_nnz, csr_val, csr_k");
+    } else {
+        return fail(KP_EINVAL, "unknown b_layout %d", d->b_layout);
+    }
+    if (d->L > 0 && (!d->S || !d->C)) return fail(KP_EINVAL, "S and C must be host arrays of length L");
+    const uint64_t allm = d->M == 64 ? ~0ull : ((1ull << d->M) - 1);
+    for (int l = 0; l < d->L; ++l) {
+        if (d->S[l] == 0) return fail(KP_EINVAL, "local set %d is empty", l);
+        if (d->S[l] & ~allm) return fail(KP_EINVAL, "local set %d names an item >= M", l);
+        if (d->C[l] < 1) return fail(KP_EINVAL, "cap C_%d must be >= 1 (Sec. 2: C_l > 0)", l);
+    }
+    // Sec. 2.1, Definition 1
+    for (int a = 0; a < d->L; ++a)
+        for (int b = a + 1; b < d->L; ++b) {
+            uint64_t i = d->S[a] & d->S[b];
+            if (i != 0 && i != d->S[a] && i != d->S[b])
+                return fail(KP_EINVAL, "local sets %d and %d are neither disjoint nor nested", a, b);
+        }
+    int cur_dev = 0;
+    KP_CUDA(cudaGetDevice(&cur_dev), "cudaGetDevice");
+
+    kp_problem *h = new (std::nothrow) kp_problem();
+    if (!h) return fail(KP_ENOMEM, "host allocation failed");
+    h->device = cur_dev;
+    kp::Params &P = h->P;
+    P.N = d->N;
+    P.M = d->M;
+    P.K = d->K;
+    P.layout = d->b_layout;
+    P.W = (d->M + 31) / 32;
+    P.p = d->p;
+    P.b = d->b_dense;
+    P.uoff = d->csr_user_off;
+    P.innz = d->csr_item_nnz;
+    P.val = d->csr_val;
+    P.kidx = d->csr_k;
+    P.B = d->B;
+    // topological order of the sets (subsets first: by size, ties by index)
+    std::vector<int> order(d->L);
+    for (int l = 0; l < d->L; ++l) order[l] = l;
+    for (int a = 1; a < d->L; ++a) {
+        int v = order[a], b = a - 1;
+        while (b >= 0 && __builtin_popcountll(d->S[order[b]]) > __builtin_popcountll(d->S[v])) {
+            order[b + 1] = order[b];
+            --b;
+        }
+        order[b + 1] = v;
+    }
+    memset(&P.tree, 0, sizeof(P.tree));
+    P.tree.L = d->L;
+    for (int t = 0; t < d->L; ++t) {
+        int l = order[t];
+        int c = d->C[l];
+        P.tree.cap[t] = (uint8_t)(c > 255 ? 255 : c);
+        for (int j = 0; j < d->M; ++j)
+            if ((d->S[l] >> j) & 1ull) P.tree.ipath[j] |= 1u << t;
+    }
+
+    kp_status st = KP_OK;
+    // device scan of the instance (Sec. 2 data assumptions)
+    uint32_t *flags = nullptr;
+    if ((st = alloc(h, &flags, 2, "validation flags")) != KP_OK) goto fail_out;
+    {
+        cudaError_t e = kp::launch_validate(P, flags, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "validate");
+            goto fail_out;
+        }
+        uint32_t hf[2] = {0, 0};
+        e = cudaMemcpy(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "validate copy");
+            goto fail_out;
+        }
+        if (hf[0]) {
+            st = fail(KP_EDATA, "instance violates Sec. 2 assumptions:%s%s%s%s%s",
+                      (hf[0] & 1) ? " p negative or non-finite;" : "",
+                      (hf[0] & 2) ? " b negative or non-finite;" : "",
+                      (hf[0] & 4) ? " csr_user_off inconsistent with csr_item_nnz;" : "",
+                      (hf[0] & 8) ? " csr_k out of range or not increasing within an item;" : "",
+                      (hf[0] & 16) ? " B_k not positive and finite;" : "");
+            goto fail_out;
+        }
+        float maxb;
+        memcpy(&maxb, &hf[1], 4);
+        double count;
+        if (P.layout == KP_B_DENSE) {
+            count = (double)P.N * P.M;
+        } else {
+            int64_t ends[2] = {0, 0};
+            e = cudaMemcpy(&ends[0], P.uoff, 8, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(&ends[1], P.uoff + P.N, 8, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "csr offsets copy");
+                goto fail_out;
+            }
+            count = (double)(ends[1] - ends[0]);
+        }
+        // fixed-point mass: every per-knapsack sum is below count * max b
+        double bound = count * (double)maxb + 1.0;
+        int s = (int)std::floor(62.0 - std::log2(bound));
+        if (s > 40) s = 40;
+        if (s < 4) s = 4;
+        P.fixs = s;
+    }
+    {
+        kp::Scratch &S = h->S;
+        S.G = kp::pass_grid_size(P);
+        const char *env = getenv("KP_BUFFER_ENTRIES");
+        double budget = env ? atof(env) : 4.0 * (double)P.N * P.M;
+        if (!env) {
+            if (budget < (double)(1 << 20)) budget = (double)(1 << 20);
+            if (budget > (double)(1 << 27)) budget = (double)(1 << 27);
+        }
+        long long cap = (long long)(budget / ((double)P.K * S.G));
+        if (cap < 64) cap = 64;
+        S.cap_kb = (int)cap;
+        const size_t K = (size_t)P.K, G = (size_t)S.G;
+        if ((st = alloc(h, &S.Rfix, K, "Rfix")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.dual_part, G, "dual partials")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.primal_part, G, "primal partials")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.hist, K * kp::NB, "histogram")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.subhist, K * kp::NSUB, "sub-histogram")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.buf, K * G * (size_t)S.cap_kb, "breakpoint buffer")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.bufcnt, K * G, "buffer counts")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.ovf, K, "overflow flags")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.sel, K, "selection state")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.ctr, 1, "counters")) != KP_OK) goto fail_out;
+        std::vector<kp::SelK> init(K);
+        for (auto &x : init) {
+            memset(&x, 0, sizeof(x));
+            x.w = kp::WMIN;
+        }
+        cudaError_t e = cudaMemcpy(S.sel, init.data(), K * sizeof(kp::SelK), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "init selection state");
+            goto fail_out;
+        }
+    }
+    *out = h;
+    return KP_OK;
+fail_out:
+    free_all(h);
+    delete h;
+    return st;
+}
+
+kp_status kp_destroy(kp_problem *h) {
+    if (!h) return KP_OK;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+    return KP_OK;
+}
+
+static kp_status state_pass(kp_problem *h, const double *lambda, uint32_t *x_bits, double *R,
+                            double *dual, double *primal, double *g, double alpha,
+                            double *lambda_next, cudaStream_t st) {
+    cudaError_t e = kp::launch_user_pass(h->P, h->S, lambda, kp::MODE_STATE, 0, x_bits, st);
+    if (e != cudaSuccess) return cuda_fail(e, "user pass");
+    e = kp::launch_finalize(h->P, h->S, lambda, R, dual, primal, g, alpha, lambda_next, st);
+    if (e != cudaSuccess) return cuda_fail(e, "finalize");
+    return KP_OK;
+}
+
+kp_status kp_solve_users(kp_problem *h, const double *lambda, uint32_t *x_bits, void *stream) {
+    if (!check_handle(h) || !lambda || !x_bits) return fail(KP_EINVAL, "kp_solve_users: NULL argument");
+    return state_pass(h, lambda, x_bits, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr,
+                      (cudaStream_t)stream);
+}
+
+kp_status kp_reduce_consumption(kp_problem *h, const double *lambda, double *R, double *dual_sum,
+                                double *primal_sum, double *g, uint32_t *x_bits, void *stream) {
+    if (!check_handle(h) || !lambda) return fail(KP_EINVAL, "kp_reduce_consumption: NULL argument");
+    return state_pass(h, lambda, x_bits, R, dual_sum, primal_sum, g, 0.0, nullptr,
+                      (cudaStream_t)stream);
+}
+
+kp_status kp_dual_value(kp_problem *h, const double *lambda, double *g, void *stream) {
+    if (!check_handle(h) || !lambda || !g) return fail(KP_EINVAL, "kp_dual_value: NULL argument");
+    return state_pass(h, lambda, nullptr, nullptr, nullptr, nullptr, g, 0.0, nullptr,
+                      (cudaStream_t)stream);
+}
+
+kp_status kp_dd_step(kp_problem *h, const double *lambda, double alpha, double *lambda_next,
+                     double *R, void *stream) {
+    if (!check_handle(h) || !lambda || !lambda_next) return fail(KP_EINVAL, "kp_dd_step: NULL argument");
+    if (!(alpha >= 0.0)) return fail(KP_EINVAL, "kp_dd_step: alpha must be >= 0");
+    return state_pass(h, lambda, nullptr, R, nullptr, nullptr, nullptr, alpha, lambda_next,
+                      (cudaStream_t)stream);
+}
+
+kp_status kp_scd_breakpoints(kp_problem *h, const double *lambda, double *R, double *dual_sum,
+                             double *primal_sum, uint32_t *x_bits, void *stream) {
+    if (!check_handle(h) || !lambda) return fail(KP_EINVAL, "kp_scd_breakpoints: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    KP_CUDA(cudaMemsetAsync(h->S.ctr, 0, offsetof(kp::Counters, status), st), "reset counters");
+    cudaError_t e = kp::launch_user_pass(h->P, h->S, lambda, kp::MODE_HIST, 0, x_bits, st);
+    if (e != cudaSuccess) return cuda_fail(e, "user pass (breakpoints)");
+    e = kp::launch_finalize(h->P, h->S, lambda, R, dual_sum, primal_sum, nullptr, 0.0, nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(e, "finalize");
+    return KP_OK;
+}
+
+kp_status kp_threshold_select(kp_problem *h, const double *lambda, double *lambda_next, void *stream) {
+    if (!check_handle(h) || !lambda || !lambda_next) return fail(KP_EINVAL, "kp_threshold_select: NULL argument");
+    if (lambda == lambda_next) return fail(KP_EINVAL, "kp_threshold_select: lambda_next must not alias lambda");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = kp::launch_select(h->P, h->S, lambda, lambda_next, 0, st);
+    if (e != cudaSuccess) return cuda_fail(e, "select");
+    for (int r = 1; r <= kp::MAX_REFINE; ++r) {
+        e = kp::launch_user_pass(h->P, h->S, lambda, kp::MODE_REFINE, r, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "user pass (refine)");
+        e = kp::launch_select(h->P, h->S, lambda, lambda_next, r, st);
+        if (e != cudaSuccess) return cuda_fail(e, "select (refine)");
+    }
+    return KP_OK;
+}
+
+kp_status kp_scd_step(kp_problem *h, const double *lambda, double *lambda_next, double *R,
+                      double *dual_sum, double *primal_sum, void *stream) {
+    kp_status s = kp_scd_breakpoints(h, lambda, R, dual_sum, primal_sum, nullptr, stream);
+    if (s != KP_OK) return s;
+    return kp_threshold_select(h, lambda, lambda_next, stream);
+}
+
+kp_status kp_dual_backward(kp_problem *h, const double *lambda, const uint32_t *x_bits,
+                           const double *R, const double *upstream, double *grad_lambda,
+                           float *grad_p, double *grad_B, void *stream) {
+    if (!check_handle(h) || !lambda || !upstream) return fail(KP_EINVAL, "kp_dual_backward: NULL argument");
+    if (grad_p && !x_bits) return fail(KP_EINVAL, "kp_dual_backward: grad_p needs x_bits");
+    if (grad_lambda && !R) return fail(KP_EINVAL, "kp_dual_backward: grad_lambda needs R");
+    cudaError_t e = kp::launch_backward(h->P, lambda, x_bits, R, upstream, grad_lambda, grad_p, grad_B,
+                                        (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "backward");
+    return KP_OK;
+}
+
+kp_status kp_device_status(kp_problem *h, void *stream) {
+    if (!check_handle(h)) return fail(KP_EINVAL, "kp_device_status: NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    KP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    int32_t status = 0;
+    KP_CUDA(cudaMemcpy(&status, &h->S.ctr->status, 4, cudaMemcpyDeviceToHost), "status copy");
+    KP_CUDA(cudaMemset(&h->S.ctr->status, 0, 4), "status reset");
+    if (status & (1 << KP_ETIMEOUT)) return fail(KP_ETIMEOUT, "a kernel's bounded wait ran out");
+    if (status & (1 << KP_ESTATE)) return fail(KP_ESTATE, "threshold selection did not converge");
+    return KP_OK;
+}
+
+kp_status kp_select_stats(kp_problem *h, int64_t out[3], void *stream) {
+    if (!check_handle(h) || !out) return fail(KP_EINVAL, "kp_select_stats: NULL argument");
+    KP_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    unsigned long long s[3];
+    KP_CUDA(cudaMemcpy(s, h->S.ctr->stats, sizeof(s), cudaMemcpyDeviceToHost), "stats copy");
+    for (int q = 0; q < 3; ++q) out[q] = (int64_t)s[q];
+    return KP_OK;
+}
+
+}  // extern "C"

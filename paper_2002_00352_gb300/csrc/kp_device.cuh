@@ -1,0 +1,355 @@
+// kp_device.cuh -- per-user device routines of the user pass.
+//
+//  greedy_walk    Algorithm 1 (Sec. 4.2) in its item-walk form: visit items by
+//                 non-increasing cost-adjusted profit p~ (ties: lower index),
+//                 accept an item if p~ > 0 and every local set containing it
+//                 still has room.  For hierarchical sets this selects exactly
+//                 the items Algorithm 1's bottom-up pass keeps.
+//  item_thresholds the value theta_j that item j's p~ must exceed for j to be
+//                 selected when only p~_j changes (matroid exchange: the best
+//                 rejected item j could swap with, or the weakest selected item
+//                 in the smallest full set containing j).
+//  sweep_k        Map of Algorithm 4 for one (user, k): the k-consumption of
+//                 the user's greedy solution as lambda_k falls from +inf to 0,
+//                 with the other multipliers fixed.  Instead of re-solving the
+//                 greedy at every candidate of Algorithm 3, the sorted order of
+//                 the positive lines z_j(lambda_k) is maintained kinetically:
+//                 consumption can only change where a line crosses zero or two
+//                 adjacent lines swap, and at such an event only the two items
+//                 involved can change membership.  Every increase is emitted as
+//                 (v1 = lambda_k at the event, v2 = increase).
+#pragma once
+#include <cfloat>
+#include <cstdint>
+
+#include "kp_internal.h"
+
+namespace kp {
+
+struct Walk {
+    uint64_t sel;   // accepted items
+    uint64_t rej;   // positive items rejected by a full set
+    uint32_t full;  // sets whose count reached their cap
+    uint64_t clo, chi;  // 8-bit counters of sets 0..7 and 8..15
+};
+
+__device__ __forceinline__ void walk_add(Walk &w, const Tree &t, int j) {
+    w.sel |= 1ull << j;
+    uint32_t path = t.ipath[j];
+    while (path) {
+        int l = __ffs(path) - 1;
+        path &= path - 1;
+        int sh = 8 * (l & 7);
+        uint32_t c;
+        if (l < 8) {
+            w.clo += 1ull << sh;
+            c = (uint32_t)(w.clo >> sh) & 0xffu;
+        } else {
+            w.chi += 1ull << sh;
+            c = (uint32_t)(w.chi >> sh) & 0xffu;
+        }
+        if (c >= t.cap[l]) w.full |= 1u << l;
+    }
+}
+
+__device__ __forceinline__ void walk_remove(Walk &w, const Tree &t, int j) {
+    w.sel &= ~(1ull << j);
+    uint32_t path = t.ipath[j];
+    while (path) {
+        int l = __ffs(path) - 1;
+        path &= path - 1;
+        int sh = 8 * (l & 7);
+        uint32_t c;
+        if (l < 8) {
+            w.clo -= 1ull << sh;
+            c = (uint32_t)(w.clo >> sh) & 0xffu;
+        } else {
+            w.chi -= 1ull << sh;
+            c = (uint32_t)(w.chi >> sh) & 0xffu;
+        }
+        if (c < t.cap[l]) w.full &= ~(1u << l);
+    }
+}
+
+// Greedy over the candidate items `cand` (all must have p~ > 0), reading p~
+// from pt[j * ps].
+__device__ __forceinline__ void greedy_walk(const float *pt, int ps, uint64_t cand, const Tree &t,
+                                            Walk &w) {
+    w.sel = 0;
+    w.rej = 0;
+    w.full = 0;
+    w.clo = 0;
+    w.chi = 0;
+    while (cand) {
+        uint64_t r = cand;
+        int best = __ffsll((long long)r) - 1;
+        float bv = pt[best * ps];
+        r &= r - 1;
+        while (r) {
+            int j = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            float v = pt[j * ps];
+            if (v > bv) {  // strict: the lower index wins ties
+                bv = v;
+                best = j;
+            }
+        }
+        cand &= ~(1ull << best);
+        if (t.ipath[best] & w.full) {
+            w.rej |= 1ull << best;
+            continue;
+        }
+        uint32_t before = w.full;
+        walk_add(w, t, best);
+        uint32_t nf = w.full & ~before;
+        if (nf) {  // items blocked by a newly full set can never be accepted
+            uint64_t r2 = cand;
+            while (r2) {
+                int j = __ffsll((long long)r2) - 1;
+                r2 &= r2 - 1;
+                if (t.ipath[j] & nf) {
+                    cand &= ~(1ull << j);
+                    w.rej |= 1ull << j;
+                }
+            }
+        }
+    }
+}
+
+// theta_j for every item given the greedy solution w over all items.
+__device__ __forceinline__ void item_thresholds(const float *pt, int M, const Walk &w,
+                                                const Tree &t, float *theta) {
+    float minSel[KP_MAX_L], maxCut[KP_MAX_L];
+    for (int l = 0; l < t.L; ++l) {
+        minSel[l] = FLT_MAX;
+        maxCut[l] = 0.f;
+    }
+    uint64_t r = w.sel;
+    while (r) {
+        int y = __ffsll((long long)r) - 1;
+        r &= r - 1;
+        float v = pt[y];
+        uint32_t path = t.ipath[y];
+        while (path) {
+            int l = __ffs(path) - 1;
+            path &= path - 1;
+            minSel[l] = fminf(minSel[l], v);
+        }
+    }
+    r = w.rej;
+    while (r) {
+        int y = __ffsll((long long)r) - 1;
+        r &= r - 1;
+        uint32_t f = t.ipath[y] & w.full;
+        if (f) {
+            int l = __ffs(f) - 1;
+            maxCut[l] = fmaxf(maxCut[l], pt[y]);
+        }
+    }
+    for (int j = 0; j < M; ++j) {
+        float th = 0.f;
+        if ((w.sel >> j) & 1ull) {
+            uint32_t path = t.ipath[j];
+            while (path) {
+                int l = __ffs(path) - 1;
+                path &= path - 1;
+                th = fmaxf(th, maxCut[l]);
+            }
+        } else {
+            uint32_t f = t.ipath[j] & w.full;
+            if (f) th = minSel[__ffs(f) - 1];
+        }
+        theta[j] = th;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// bucket / key / fixed-point helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t key_of(float v) {
+    uint32_t k = __float_as_uint(v);
+    return k > 0x7F7FFFFFu ? 0x7F7FFFFFu : k;
+}
+
+__device__ __forceinline__ int bucket_of(uint32_t key, uint32_t ckey) {
+    long long d = (long long)key - (long long)ckey;
+    if (d == 0) return NB_CENTRE;
+    unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+    int e = 63 - __clzll((long long)ad);
+    return d > 0 ? NB_CENTRE + 1 + e : NB_CENTRE - 1 - e;
+}
+
+__device__ __forceinline__ unsigned long long fixmass(float v, float scale) {
+    return __float2ull_rn(v * scale);
+}
+
+// ---------------------------------------------------------------------------
+// Map of Algorithm 4 for one (user, k).
+//   pt[j*ps]   p~_j at lambda^t;  s[j*ss]  b_jk (0 for items not in J)
+//   J          items with b_jk > 0 (the lines that move with lambda_k)
+//   lamk       lambda_k^t in FP32
+// ---------------------------------------------------------------------------
+template <int MAXM, class Sink>
+__device__ void sweep_k(const float *pt, int ps, const float *s, int ss, int M, uint64_t J,
+                        float lamk, const Tree &t, int k, Sink &sink) {
+    float la[MAXM], ls[MAXM], zc[MAXM], pe[MAXM];
+    int ord[MAXM], zl[MAXM];
+
+    // items whose line does not move: only the greedy selection among them at
+    // lambda_k = +inf can ever be selected (no fixed item can enter later)
+    uint64_t fcand = 0;
+    for (int j = 0; j < M; ++j)
+        if (!((J >> j) & 1ull) && pt[j * ps] > 0.f) fcand |= 1ull << j;
+    Walk w;
+    greedy_walk(pt, ps, fcand, t, w);
+
+    int np = 0;
+    uint64_t r = w.sel;
+    while (r) {  // positive fixed lines, by p~ descending (ties: lower index)
+        uint64_t q = r;
+        int best = __ffsll((long long)q) - 1;
+        float bv = pt[best * ps];
+        q &= q - 1;
+        while (q) {
+            int j = __ffsll((long long)q) - 1;
+            q &= q - 1;
+            float v = pt[j * ps];
+            if (v > bv) {
+                bv = v;
+                best = j;
+            }
+        }
+        r &= ~(1ull << best);
+        la[best] = bv;
+        ls[best] = 0.f;
+        ord[np++] = best;
+    }
+    for (int q = 0; q + 1 < np; ++q) pe[q] = -1.f;
+
+    int nz = 0;
+    uint64_t mj = J;
+    while (mj) {
+        int j = __ffsll((long long)mj) - 1;
+        mj &= mj - 1;
+        float sj = s[j * ss];
+        float a = fmaf(lamk, sj, pt[j * ps]);
+        la[j] = a;
+        ls[j] = sj;
+        if (a > 0.f) {
+            float z = a / sj;
+            zc[j] = z;
+            int pos = nz++;  // insertion by zero crossing, descending
+            while (pos > 0 && zc[zl[pos - 1]] < z) {
+                zl[pos] = zl[pos - 1];
+                --pos;
+            }
+            zl[pos] = j;
+        }
+    }
+
+    auto pair_ev = [&](int up, int low, float cur) -> float {
+        float dsl = ls[low] - ls[up];
+        if (!(dsl > 0.f)) return -1.f;
+        float x = (la[low] - la[up]) / dsl;
+        if (x > cur) x = cur;
+        return x > 0.f ? x : -1.f;
+    };
+
+    float cur = FLT_MAX;
+    int zi = 0;
+    const int guard = M * M + 2 * M + 2;
+    for (int it = 0; it < guard; ++it) {
+        float bs = -1.f;
+        int bq = -1;
+        for (int q = 0; q + 1 < np; ++q)
+            if (pe[q] > bs) {
+                bs = pe[q];
+                bq = q;
+            }
+        float bz = zi < nz ? zc[zl[zi]] : -1.f;
+        if (bz <= 0.f && bs <= 0.f) break;
+        if (bz >= bs) {
+            cur = bz;
+            int j = zl[zi++];
+            ord[np++] = j;
+            if (np >= 2) pe[np - 2] = pair_ev(ord[np - 2], j, cur);
+            if ((t.ipath[j] & w.full) == 0) {
+                walk_add(w, t, j);
+                sink.emit(k, cur, ls[j]);
+            }
+        } else {
+            cur = bs;
+            int u = ord[bq], v = ord[bq + 1];
+            ord[bq] = v;
+            ord[bq + 1] = u;
+            pe[bq] = -1.f;
+            if (bq > 0) pe[bq - 1] = pair_ev(ord[bq - 1], v, cur);
+            if (bq + 2 < np) pe[bq + 1] = pair_ev(u, ord[bq + 2], cur);
+            if (((w.sel >> u) & 1ull) && !((w.sel >> v) & 1ull)) {
+                uint32_t f = t.ipath[v] & w.full;
+                if (f) {
+                    int tl = __ffs(f) - 1;
+                    if ((t.ipath[u] >> tl) & 1u) {
+                        walk_remove(w, t, u);
+                        walk_add(w, t, v);
+                        sink.emit(k, cur, ls[v] - ls[u]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// emission sinks
+// ---------------------------------------------------------------------------
+// First pass: log histogram around the centre + buffered window.
+struct HistSink {
+    unsigned long long *hist;  // [K][NB] (shared or global memory)
+    const uint32_t *ckey;      // [K]
+    const int32_t *wwin;       // [K]
+    uint32_t *bcnt;            // [K] buffer fill of this block
+    uint2 *buf;
+    int cap_kb, G, blk;
+    float scale;
+    __device__ __forceinline__ void emit(int k, float v1, float v2) {
+        if (!(v1 > 0.f) || !(v2 > 0.f)) return;
+        uint32_t key = key_of(v1);
+        int b = bucket_of(key, ckey[k]);
+        atomicAdd(&hist[(size_t)k * NB + b], fixmass(v2, scale));
+        int off = b - NB_CENTRE;
+        if (off < 0) off = -off;
+        if (off <= wwin[k]) {
+            uint32_t slot = atomicAdd(&bcnt[k], 1u);
+            if (slot < (uint32_t)cap_kb)
+                buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key, __float_as_uint(v2));
+        }
+    }
+};
+
+// Refine pass: sub-histogram of the unresolved range + buffer of its entries.
+struct RefineSink {
+    const uint32_t *lo, *hi;   // [K]; empty range for resolved knapsacks
+    const int32_t *shift;      // [K]
+    unsigned long long *subhist;  // [K][NSUB] global
+    uint32_t *bcnt;
+    uint2 *buf;
+    int cap_kb, G, blk;
+    float scale;
+    __device__ __forceinline__ void emit(int k, float v1, float v2) {
+        if (!(v1 > 0.f) || !(v2 > 0.f)) return;
+        uint32_t key = key_of(v1);
+        if (key < lo[k] || key >= hi[k]) return;
+        int sb = (int)((key - lo[k]) >> shift[k]);
+        atomicAdd(&subhist[(size_t)k * NSUB + sb], fixmass(v2, scale));
+        uint32_t slot = atomicAdd(&bcnt[k], 1u);
+        if (slot < (uint32_t)cap_kb)
+            buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key, __float_as_uint(v2));
+    }
+};
+
+struct NullSink {
+    __device__ __forceinline__ void emit(int, float, float) {}
+};
+
+}  // namespace kp

@@ -62,24 +62,27 @@ class Instance:
 
     def users_dense(self, idx) -> tuple:
         """(p [n, M], b [n, M, K]) as float64 numpy arrays for the given users."""
-        idx = torch.as_tensor(np.asarray(idx, dtype=np.int64))
+        dev = self.p.device
+        idx = torch.as_tensor(np.asarray(idx, dtype=np.int64), device=dev)
         M, K = self.M, self.K
-        p = self.p.view(self.N, M)[idx.to(self.p.device)].double().cpu().numpy()
+        n = idx.numel()
+        p = self.p.view(self.N, M)[idx].double().cpu().numpy()
         if self.layout == "dense":
-            b = self.b.view(self.N, M, K)[idx.to(self.b.device)].double().cpu().numpy()
+            b = self.b.view(self.N, M, K)[idx].double().cpu().numpy()
             return p, b
-        off = self.user_off.cpu().numpy()
-        nnz = self.item_nnz.view(self.N, M).cpu().numpy() if idx.numel() > 4096 else None
-        b = np.zeros((idx.numel(), M, K))
-        for r, i in enumerate(idx.tolist()):
-            e0, e1 = int(off[i]), int(off[i + 1])
-            vals = self.val[e0:e1].double().cpu().numpy()
-            ks = self.kidx[e0:e1].long().cpu().numpy()
-            cnt = (nnz[i] if nnz is not None else
-                   self.item_nnz[i * M:(i + 1) * M].cpu().numpy()).astype(np.int64)
-            owner = np.repeat(np.arange(M), cnt)
-            np.add.at(b[r], (owner, ks), vals)
-        return p, b
+        # gather the users' CSR entries (layout conversion only)
+        starts = self.user_off[idx]
+        cnt = self.item_nnz.view(self.N, M)[idx].long()          # [n, M]
+        tot = cnt.sum(1)                                          # [n]
+        nent = int(tot.sum())
+        b = torch.zeros(n * M, K, dtype=torch.float64, device=dev)
+        if nent:
+            base = torch.repeat_interleave(starts, tot)
+            first = torch.repeat_interleave(torch.cumsum(tot, 0) - tot, tot)
+            ent = base + (torch.arange(nent, device=dev) - first)
+            owner = torch.repeat_interleave(torch.arange(n * M, device=dev), cnt.reshape(-1))
+            b.index_put_((owner, self.kidx[ent].long()), self.val[ent].double(), accumulate=True)
+        return p, b.view(n, M, K).cpu().numpy()
 
     def to_dense_numpy(self) -> tuple:
         """(p [N, M], b [N, M, K]) float64 numpy for the whole (small) instance."""

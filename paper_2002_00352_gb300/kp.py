@@ -1,0 +1,252 @@
+"""Thin Python binding of the C ABI in include/kp.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls, takes torch CUDA
+tensors and passes their device pointers and the current CUDA stream.  All
+computation happens in libkp.so; if the library is not built or not loadable
+the import of this module's functions raises (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkp.so")
+
+KP_OK, KP_EINVAL, KP_ENOMEM, KP_ECUDA, KP_ETIMEOUT, KP_ESTATE, KP_EDATA = range(7)
+KP_B_DENSE, KP_B_CSR = 0, 1
+_STATUS = {0: "KP_OK", 1: "KP_EINVAL", 2: "KP_ENOMEM", 3: "KP_ECUDA", 4: "KP_ETIMEOUT",
+           5: "KP_ESTATE", 6: "KP_EDATA"}
+
+_lib = None
+
+
+class KpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kp_desc(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int64),
+        ("M", ctypes.c_int32),
+        ("K", ctypes.c_int32),
+        ("p", ctypes.c_void_p),
+        ("b_layout", ctypes.c_int32),
+        ("b_dense", ctypes.c_void_p),
+        ("csr_user_off", ctypes.c_void_p),
+        ("csr_item_nnz", ctypes.c_void_p),
+        ("csr_val", ctypes.c_void_p),
+        ("csr_k", ctypes.c_void_p),
+        ("B", ctypes.c_void_p),
+        ("L", ctypes.c_int32),
+        ("S", ctypes.c_void_p),
+        ("C", ctypes.c_void_p),
+    ]
+
+
+EXPORTS = [
+    "kp_create", "kp_destroy", "kp_solve_users", "kp_reduce_consumption", "kp_dual_value",
+    "kp_dd_step", "kp_scd_breakpoints", "kp_threshold_select", "kp_scd_step",
+    "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_last_error", "kp_version",
+]
+
+
+def load_library(path: Optional[str] = None):
+    """Load libkp.so (raises OSError if it is missing: nothing falls back to the CPU)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    lib = ctypes.CDLL(path or LIB_PATH)
+    P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    lib.kp_create.argtypes = [ctypes.POINTER(kp_desc), ctypes.POINTER(ctypes.c_void_p)]
+    lib.kp_destroy.argtypes = [P]
+    lib.kp_solve_users.argtypes = [P, P, P, P]
+    lib.kp_reduce_consumption.argtypes = [P, P, P, P, P, P, P, P]
+    lib.kp_dual_value.argtypes = [P, P, P, P]
+    lib.kp_dd_step.argtypes = [P, P, f64, P, P, P]
+    lib.kp_scd_breakpoints.argtypes = [P, P, P, P, P, P, P]
+    lib.kp_threshold_select.argtypes = [P, P, P, P]
+    lib.kp_scd_step.argtypes = [P, P, P, P, P, P, P]
+    lib.kp_dual_backward.argtypes = [P, P, P, P, P, P, P, P, P]
+    lib.kp_device_status.argtypes = [P, P]
+    lib.kp_select_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
+    lib.kp_last_error.restype = ctypes.c_char_p
+    lib.kp_version.restype = ctypes.c_int
+    for name in EXPORTS:
+        if name not in ("kp_last_error", "kp_version"):
+            getattr(lib, name).restype = i32
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != KP_OK:
+        raise KpError(status, load_library().kp_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None, name=""):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Problem:
+    """A kp_problem handle plus references to the borrowed instance tensors."""
+
+    def __init__(self, handle, N, M, K, layout, keep):
+        self.handle = handle
+        self.N, self.M, self.K, self.layout = N, M, K, layout
+        self.W = (M + 31) // 32
+        self._keep = keep
+
+    def close(self):
+        if self.handle:
+            load_library().kp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kp_create(N: int, M: int, K: int, p: torch.Tensor, B: torch.Tensor, S: Sequence[int],
+              C: Sequence[int], b_dense: Optional[torch.Tensor] = None,
+              csr_user_off: Optional[torch.Tensor] = None,
+              csr_item_nnz: Optional[torch.Tensor] = None,
+              csr_val: Optional[torch.Tensor] = None,
+              csr_k: Optional[torch.Tensor] = None) -> Problem:
+    lib = load_library()
+    d = kp_desc()
+    d.N, d.M, d.K = int(N), int(M), int(K)
+    d.p = _ptr(p, torch.float32, "p")
+    d.B = _ptr(B, torch.float64, "B")
+    if b_dense is not None:
+        d.b_layout = KP_B_DENSE
+        d.b_dense = _ptr(b_dense, torch.float32, "b_dense")
+    else:
+        d.b_layout = KP_B_CSR
+        d.csr_user_off = _ptr(csr_user_off, torch.int64, "csr_user_off")
+        d.csr_item_nnz = _ptr(csr_item_nnz, torch.uint8, "csr_item_nnz")
+        d.csr_val = _ptr(csr_val, torch.float32, "csr_val")
+        d.csr_k = _ptr(csr_k, torch.int16, "csr_k")
+    Sa = (ctypes.c_uint64 * max(1, len(S)))(*[int(s) for s in S])
+    Ca = (ctypes.c_int32 * max(1, len(C)))(*[int(c) for c in C])
+    d.L = len(S)
+    d.S = ctypes.cast(Sa, ctypes.c_void_p)
+    d.C = ctypes.cast(Ca, ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    _check(lib.kp_create(ctypes.byref(d), ctypes.byref(h)))
+    keep = (p, B, b_dense, csr_user_off, csr_item_nnz, csr_val, csr_k)
+    return Problem(h, int(N), int(M), int(K), d.b_layout, keep)
+
+
+def kp_create_from_instance(inst) -> Problem:
+    """kp_create for a paper_2002_00352_gb300.gen.Instance on a CUDA device."""
+    if inst.layout == "dense":
+        return kp_create(inst.N, inst.M, inst.K, inst.p, inst.B, inst.S, inst.C, b_dense=inst.b)
+    return kp_create(inst.N, inst.M, inst.K, inst.p, inst.B, inst.S, inst.C,
+                     csr_user_off=inst.user_off, csr_item_nnz=inst.item_nnz, csr_val=inst.val,
+                     csr_k=inst.kidx)
+
+
+def _x_bits(prob: Problem, x_bits):
+    if x_bits is None:
+        x_bits = torch.empty(prob.N * prob.W, dtype=torch.int32, device="cuda")
+    return x_bits
+
+
+def kp_solve_users(prob: Problem, lam: torch.Tensor, x_bits=None, stream=None) -> torch.Tensor:
+    x_bits = _x_bits(prob, x_bits)
+    _check(load_library().kp_solve_users(prob.handle, _ptr(lam, torch.float64, "lambda"),
+                                         _ptr(x_bits, None, "x_bits"), _stream(stream)))
+    return x_bits
+
+
+def kp_reduce_consumption(prob: Problem, lam, R=None, dual_sum=None, primal_sum=None, g=None,
+                          x_bits=None, stream=None):
+    _check(load_library().kp_reduce_consumption(
+        prob.handle, _ptr(lam, torch.float64, "lambda"), _ptr(R, torch.float64, "R"),
+        _ptr(dual_sum, torch.float64, "dual_sum"), _ptr(primal_sum, torch.float64, "primal_sum"),
+        _ptr(g, torch.float64, "g"), _ptr(x_bits, None, "x_bits"), _stream(stream)))
+
+
+def kp_dual_value(prob: Problem, lam, g, stream=None):
+    _check(load_library().kp_dual_value(prob.handle, _ptr(lam, torch.float64, "lambda"),
+                                        _ptr(g, torch.float64, "g"), _stream(stream)))
+
+
+def kp_dd_step(prob: Problem, lam, alpha: float, lam_next, R=None, stream=None):
+    _check(load_library().kp_dd_step(prob.handle, _ptr(lam, torch.float64, "lambda"), float(alpha),
+                                     _ptr(lam_next, torch.float64, "lambda_next"),
+                                     _ptr(R, torch.float64, "R"), _stream(stream)))
+
+
+def kp_scd_breakpoints(prob: Problem, lam, R=None, dual_sum=None, primal_sum=None, x_bits=None,
+                       stream=None):
+    _check(load_library().kp_scd_breakpoints(
+        prob.handle, _ptr(lam, torch.float64, "lambda"), _ptr(R, torch.float64, "R"),
+        _ptr(dual_sum, torch.float64, "dual_sum"), _ptr(primal_sum, torch.float64, "primal_sum"),
+        _ptr(x_bits, None, "x_bits"), _stream(stream)))
+
+
+def kp_threshold_select(prob: Problem, lam, lam_next, stream=None):
+    _check(load_library().kp_threshold_select(prob.handle, _ptr(lam, torch.float64, "lambda"),
+                                              _ptr(lam_next, torch.float64, "lambda_next"),
+                                              _stream(stream)))
+
+
+def kp_scd_step(prob: Problem, lam, lam_next, R=None, dual_sum=None, primal_sum=None, stream=None):
+    _check(load_library().kp_scd_step(
+        prob.handle, _ptr(lam, torch.float64, "lambda"), _ptr(lam_next, torch.float64, "lambda_next"),
+        _ptr(R, torch.float64, "R"), _ptr(dual_sum, torch.float64, "dual_sum"),
+        _ptr(primal_sum, torch.float64, "primal_sum"), _stream(stream)))
+
+
+def kp_dual_backward(prob: Problem, lam, x_bits, R, upstream, grad_lambda=None, grad_p=None,
+                     grad_B=None, stream=None):
+    _check(load_library().kp_dual_backward(
+        prob.handle, _ptr(lam, torch.float64, "lambda"), _ptr(x_bits, None, "x_bits"),
+        _ptr(R, torch.float64, "R"), _ptr(upstream, torch.float64, "upstream"),
+        _ptr(grad_lambda, torch.float64, "grad_lambda"), _ptr(grad_p, torch.float32, "grad_p"),
+        _ptr(grad_B, torch.float64, "grad_B"), _stream(stream)))
+
+
+def kp_device_status(prob: Problem, stream=None):
+    _check(load_library().kp_device_status(prob.handle, _stream(stream)))
+
+
+def kp_select_stats(prob: Problem, stream=None):
+    out = (ctypes.c_int64 * 3)()
+    _check(load_library().kp_select_stats(prob.handle, out, _stream(stream)))
+    return list(out)
+
+
+def kp_version() -> int:
+    return int(load_library().kp_version())
+
+
+def unpack_x(x_bits: torch.Tensor, N: int, M: int) -> torch.Tensor:
+    """x bits (int32 words, W per user) -> uint8 [N, M] tensor on the same device."""
+    W = (M + 31) // 32
+    w = x_bits.view(N, W).to(torch.int64) & 0xFFFFFFFF
+    j = torch.arange(M, device=x_bits.device)
+    return ((w[:, j // 32] >> (j % 32)) & 1).to(torch.uint8)

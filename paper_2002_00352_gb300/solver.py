@@ -1,0 +1,88 @@
+"""Iteration drivers over the C ABI: dual descent (Algorithm 2) and synchronous
+coordinate descent (Algorithm 4), eager or replayed from a CUDA graph.
+
+Each iteration is a fixed sequence of library calls on the current stream;
+nothing here computes any part of the method.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import kp
+
+
+class IterStats:
+    """Per-iteration device outputs: R [K], dual sum, primal sum (float64, on device)."""
+
+    def __init__(self, K: int, device):
+        self.R = torch.zeros(K, dtype=torch.float64, device=device)
+        self.dual = torch.zeros((), dtype=torch.float64, device=device)
+        self.primal = torch.zeros((), dtype=torch.float64, device=device)
+
+
+def dd_step(prob, lam, alpha, lam_next, stats: IterStats = None):
+    kp.kp_dd_step(prob, lam, alpha, lam_next, R=stats.R if stats else None)
+
+
+def scd_step(prob, lam, lam_next, stats: IterStats = None):
+    if stats is None:
+        kp.kp_scd_step(prob, lam, lam_next)
+    else:
+        kp.kp_scd_step(prob, lam, lam_next, R=stats.R, dual_sum=stats.dual, primal_sum=stats.primal)
+
+
+def scd_solve(prob, lam0: torch.Tensor, iters: int, record: bool = False):
+    """Runs `iters` SCD iterations from lam0; returns the final lambda and, if
+    `record`, the list of lambdas (host float64 tensors)."""
+    a = lam0.clone()
+    b = torch.empty_like(a)
+    hist = [a.cpu()] if record else None
+    for _ in range(iters):
+        scd_step(prob, a, b)
+        a, b = b, a
+        if record:
+            hist.append(a.cpu())
+    return a, hist
+
+
+def dd_solve(prob, lam0: torch.Tensor, alpha: float, iters: int, record: bool = False):
+    a = lam0.clone()
+    b = torch.empty_like(a)
+    hist = [a.cpu()] if record else None
+    for _ in range(iters):
+        dd_step(prob, a, alpha, b)
+        a, b = b, a
+        if record:
+            hist.append(a.cpu())
+    return a, hist
+
+
+class ScdGraph:
+    """Two SCD iterations (lambda_a -> lambda_b -> lambda_a) captured in one CUDA
+    graph; replay() advances the state by two iterations with one launch."""
+
+    def __init__(self, prob, lam0: torch.Tensor, stats: IterStats = None):
+        self.prob = prob
+        self.a = lam0.clone()
+        self.b = torch.empty_like(self.a)
+        self.stats = stats
+        # warm up outside capture (first launches set kernel attributes)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            tmp = self.a.clone()
+            tmp2 = torch.empty_like(tmp)
+            scd_step(prob, tmp, tmp2, stats)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            scd_step(prob, self.a, self.b, stats)
+            scd_step(prob, self.b, self.a, stats)
+
+    def replay(self):
+        self.graph.replay()
+
+    @property
+    def lam(self):
+        return self.a

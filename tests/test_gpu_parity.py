@@ -1,0 +1,299 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Every test here needs a GB300 and the built libkp.so; inputs are the seeded
+generators of paper_2002_00352_gb300.gen, created on the GPU and copied to the
+host for the oracle.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2002_00352_gb300 import gen, kp
+from tests.gpu_util import REL_LAMBDA, compare_state, cuda_state, lam_close
+from tests.helpers import random_laminar
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _problem(inst):
+    return kp.kp_create_from_instance(inst)
+
+
+def _dense_np(inst):
+    return inst.to_dense_numpy()
+
+
+# ---------------------------------------------------------------------------
+# decisions, consumption, objectives at fixed lambda (Algorithm 1 + Algorithm 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("layout", ["dense", "csr"])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_state_parity_random_trees(layout, seed):
+    rng = np.random.default_rng(seed)
+    M = int(rng.integers(2, 14))
+    K = int(rng.integers(1, 9))
+    S, C = random_laminar(M, rng, max_nodes=6)
+    N = 3001
+    inst = gen.random_small(N, M, K, seed=seed, device="cuda", layout=layout)
+    inst.S, inst.C = S, C
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    for trial in range(4):
+        lam = rng.uniform(0, 0.6, size=K) * (rng.random(K) < 0.8)
+        x, R, d, pr, g, _ = cuda_state(prob, torch.tensor(lam, device="cuda"))
+        xo, Ro, do, po = oracle.user_pass(p, b, S, C, lam)
+        compare_state(p, b, lam, x, R, d, pr, xo, Ro, do, po)
+        assert g == pytest.approx(d + float(lam @ inst.B.cpu().numpy()), rel=1e-12)
+
+
+def test_state_parity_small_config():
+    inst = gen.small_dd_scd(device="cuda")
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    rng = np.random.default_rng(0)
+    for lam in [np.zeros(5), rng.uniform(0, 1, 5), np.full(5, 0.66), np.full(5, 50.0)]:
+        x, R, d, pr, g, _ = cuda_state(prob, torch.tensor(lam, device="cuda"))
+        xo, Ro, do, po = oracle.user_pass(p, b, inst.S, inst.C, lam)
+        compare_state(p, b, lam, x, R, d, pr, xo, Ro, do, po)
+
+
+def test_state_parity_sparse_config_downscaled():
+    inst = gen.sparse_csr(N=20_000, device="cuda")
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    rng = np.random.default_rng(5)
+    lam = rng.uniform(0, 8, size=inst.K)
+    x, R, d, pr, g, _ = cuda_state(prob, torch.tensor(lam, device="cuda"))
+    xo, Ro, do, po = oracle.user_pass(p, b, inst.S, inst.C, lam)
+    compare_state(p, b, lam, x, R, d, pr, xo, Ro, do, po)
+
+
+# ---------------------------------------------------------------------------
+# one SCD iteration (Algorithms 3-4) at the same lambda^t
+# ---------------------------------------------------------------------------
+
+def _scd_gpu(prob, lam):
+    lt = torch.tensor(lam, dtype=torch.float64, device="cuda")
+    ln = torch.zeros_like(lt)
+    kp.kp_scd_step(prob, lt, ln)
+    kp.kp_device_status(prob)
+    return ln.cpu().numpy()
+
+
+@pytest.mark.parametrize("layout", ["dense", "csr"])
+@pytest.mark.parametrize("seed", [11, 12, 13, 14])
+def test_scd_step_parity_random(layout, seed):
+    rng = np.random.default_rng(seed)
+    M = int(rng.integers(2, 11))
+    K = int(rng.integers(1, 7))
+    S, C = random_laminar(M, rng, max_nodes=5)
+    inst = gen.random_small(2000, M, K, seed=seed, device="cuda", layout=layout, frac=0.15)
+    inst.S, inst.C = S, C
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    B = inst.B.cpu().numpy()
+    for trial in range(3):
+        lam = rng.uniform(0, 0.8, size=K) * (rng.random(K) < 0.8)
+        got = _scd_gpu(prob, lam)
+        want, _, _ = oracle.scd_step(p, b, S, C, lam, B)
+        assert np.all(lam_close(got, want)), (got, want)
+
+
+def test_scd_trajectory_small_config():
+    """N=1e4, M=10, K=5: 50 SCD iterations; each GPU step matches the oracle's step
+    taken at the GPU's own lambda^t."""
+    inst = gen.small_dd_scd(device="cuda")
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    B = inst.B.cpu().numpy()
+    lam = np.zeros(inst.K)
+    for t in range(50):
+        got = _scd_gpu(prob, lam)
+        if t < 6 or t % 7 == 0:
+            want, _, _ = oracle.scd_step(p, b, inst.S, inst.C, lam, B)
+            assert np.all(lam_close(got, want)), (t, got, want)
+        lam = got
+
+
+def test_scd_step_sparse_downscaled():
+    inst = gen.sparse_csr(N=20_000, device="cuda")
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    B = inst.B.cpu().numpy()
+    lam = np.zeros(inst.K)
+    for t in range(4):
+        got = _scd_gpu(prob, lam)
+        want, _, _ = oracle.scd_step(p, b, inst.S, inst.C, lam, B)
+        frac_ok = lam_close(got, want).mean()
+        assert frac_ok == 1.0, (t, frac_ok, np.max(np.abs(got - want) / np.maximum(want, 1e-12)))
+        lam = got
+
+
+def test_dd_trajectory_small_config():
+    """Eq. (14): 50 DD iterations at alpha = 1e-3 (Sec. 6.5's learning rates)."""
+    inst = gen.small_dd_scd(device="cuda")
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    B = inst.B.cpu().numpy()
+    lam_t = torch.zeros(inst.K, dtype=torch.float64, device="cuda")
+    nxt = torch.zeros_like(lam_t)
+    R = torch.zeros_like(lam_t)
+    for t in range(50):
+        kp.kp_dd_step(prob, lam_t, 1e-3, nxt, R=R)
+        lam = lam_t.cpu().numpy()
+        _, Ro, _, _ = oracle.user_pass(p, b, inst.S, inst.C, lam, want_x=False)
+        want = oracle.dd_update(lam, Ro, B, 1e-3)
+        got = nxt.cpu().numpy()
+        # one excused item changes R by at most max b <= 1, i.e. lambda by alpha
+        assert np.all(np.abs(got - want) <= 1e-6 * np.abs(want) + 1e-3 * 2.0), (t, got, want)
+        lam_t.copy_(nxt)
+
+
+def test_golden_fixture():
+    d = json.load(open(os.path.join(HERE, "golden", "oracle_tiny.json")))
+    N, M, K = d["N"], d["M"], d["K"]
+    p = torch.tensor(d["p"], dtype=torch.float32, device="cuda")
+    b = torch.tensor(d["b"], dtype=torch.float32, device="cuda")
+    B = torch.tensor(d["B"], dtype=torch.float64, device="cuda")
+    prob = kp.kp_create(N, M, K, p, B, d["S"], d["C"], b_dense=b)
+    lam = np.zeros(K)
+    for t in range(1, len(d["scd_lambda"])):
+        lam = _scd_gpu(prob, lam)
+        assert np.all(lam_close(lam, d["scd_lambda"][t])), (t, lam, d["scd_lambda"][t])
+    lt = torch.zeros(K, dtype=torch.float64, device="cuda")
+    nx = torch.zeros_like(lt)
+    for t in range(1, len(d["dd_lambda"])):
+        kp.kp_dd_step(prob, lt, d["alpha"], nx)
+        lt.copy_(nx)
+        assert np.all(np.abs(lt.cpu().numpy() - np.array(d["dd_lambda"][t])) <= 1e-9 + 1e-6 * np.abs(d["dd_lambda"][t]))
+
+
+# ---------------------------------------------------------------------------
+# dual gradient (Danskin) and the autograd function
+# ---------------------------------------------------------------------------
+
+def test_dual_backward_matches_oracle_and_fd():
+    from paper_2002_00352_gb300.autograd import dual
+    inst = gen.dense_2e7(N=50_000, device="cuda")
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    B = inst.B.cpu().numpy()
+    rng = np.random.default_rng(3)
+    inst.p.requires_grad_(True)
+    inst.B.requires_grad_(True)
+    for trial in range(64):
+        lam0 = rng.uniform(0.05, 0.2, size=inst.K)
+        lam = torch.tensor(lam0, device="cuda", requires_grad=True)
+        g = dual(lam, prob)
+        (gl, gp, gB) = torch.autograd.grad(2.0 * g, [lam, inst.p, inst.B])
+        if trial < 3:
+            x, R, _, _ = oracle.user_pass(p, b, inst.S, inst.C, lam0)
+            assert np.allclose(gl.cpu().numpy(), 2.0 * (B - R), rtol=1e-6, atol=2.0 * 1.0)
+            assert np.allclose(gB.cpu().numpy(), 2.0 * lam0)
+            xm = gp.detach().cpu().numpy().reshape(inst.N, inst.M) / 2.0
+            assert (xm != x).any(axis=1).sum() <= 5
+        # central differences of the GPU dual at h = 1e-4
+        h = 1e-4
+        k = trial % inst.K
+        e = np.zeros(inst.K)
+        e[k] = h
+        gv = torch.zeros((), dtype=torch.float64, device="cuda")
+        kp.kp_dual_value(prob, torch.tensor(lam0 + e, device="cuda"), gv)
+        gp_ = float(gv)
+        kp.kp_dual_value(prob, torch.tensor(lam0 - e, device="cuda"), gv)
+        gm_ = float(gv)
+        fd = (gp_ - gm_) / (2 * h)
+        assert fd == pytest.approx(float(gl[k]) / 2.0, rel=1e-3, abs=2.0)
+
+
+# ---------------------------------------------------------------------------
+# edge cases and errors
+# ---------------------------------------------------------------------------
+
+def test_edge_single_user_single_item():
+    p = torch.tensor([0.6], dtype=torch.float32, device="cuda")
+    b = torch.tensor([0.3], dtype=torch.float32, device="cuda")
+    B = torch.tensor([0.1], dtype=torch.float64, device="cuda")
+    prob = kp.kp_create(1, 1, 1, p, B, [], [], b_dense=b)
+    got = _scd_gpu(prob, np.zeros(1))
+    assert got[0] == pytest.approx(2.0, rel=1e-6)   # zero crossing p/b
+    x, R, d, pr, g, _ = cuda_state(prob, torch.tensor([2.5], dtype=torch.float64, device="cuda"))
+    assert x.sum() == 0 and R[0] == 0.0
+
+
+def test_edge_empty_csr_rows_and_zero_entries():
+    N, M, K = 5, 4, 3
+    p = torch.rand(N * M, device="cuda")
+    nnz = torch.tensor([0, 0, 0, 0, 1, 0, 2, 0, 0, 0, 0, 0, 3, 1, 0, 0, 0, 0, 0, 1],
+                       dtype=torch.uint8, device="cuda")
+    cnt = nnz.long().view(N, M).sum(1)
+    off = torch.zeros(N + 1, dtype=torch.int64, device="cuda")
+    off[1:] = torch.cumsum(cnt, 0)
+    ks = torch.tensor([2, 0, 1, 0, 1, 2, 1, 0], dtype=torch.int16, device="cuda")
+    vals = torch.tensor([0.5, 0.0, 0.7, 0.2, 0.3, 0.9, 0.4, 0.6], device="cuda")
+    B = torch.tensor([0.5, 0.5, 0.5], dtype=torch.float64, device="cuda")
+    prob = kp.kp_create(N, M, K, p, B, [0b1111], [2], csr_user_off=off, csr_item_nnz=nnz,
+                        csr_val=vals, csr_k=ks)
+    dense = oracle.densify_csr(N, M, K, off.cpu(), nnz.cpu(), vals.cpu(), ks.cpu())
+    pn = p.cpu().double().numpy().reshape(N, M)
+    lam = np.array([0.3, 0.0, 1.2])
+    x, R, d, pr, g, _ = cuda_state(prob, torch.tensor(lam, device="cuda"))
+    xo, Ro, do, po = oracle.user_pass(pn, dense, [0b1111], [2], lam)
+    compare_state(pn, dense, lam, x, R, d, pr, xo, Ro, do, po)
+    got = _scd_gpu(prob, lam)
+    want, _, _ = oracle.scd_step(pn, dense, [0b1111], [2], lam, B.cpu().numpy())
+    assert np.all(lam_close(got, want))
+
+
+def test_errors_are_reported():
+    p = torch.rand(8, device="cuda")
+    b = torch.rand(8 * 2, device="cuda")
+    B = torch.ones(2, dtype=torch.float64, device="cuda")
+    with pytest.raises(kp.KpError) as e:
+        kp.kp_create(2, 4, 2, p, B, [0b0011, 0b0110], [1, 1], b_dense=b)   # not hierarchical
+    assert e.value.status == kp.KP_EINVAL
+    with pytest.raises(kp.KpError) as e:
+        kp.kp_create(2, 4, 2, p, B, [0b0011], [0], b_dense=b)              # C_l must be > 0
+    assert e.value.status == kp.KP_EINVAL
+    bneg = b.clone()
+    bneg[3] = -1.0
+    with pytest.raises(kp.KpError) as e:
+        kp.kp_create(2, 4, 2, p, B, [0b0011], [1], b_dense=bneg)           # b >= 0 (Sec. 2)
+    assert e.value.status == kp.KP_EDATA
+    with pytest.raises(kp.KpError) as e:
+        kp.kp_create(2, 65, 2, p, B, [], [], b_dense=b)                    # M > 64
+    assert e.value.status == kp.KP_EINVAL
+
+
+def test_determinism():
+    inst = gen.small_dd_scd(device="cuda")
+    prob = _problem(inst)
+    lam = torch.full((inst.K,), 0.4, dtype=torch.float64, device="cuda")
+    outs = []
+    for _ in range(2):
+        R = torch.zeros(inst.K, dtype=torch.float64, device="cuda")
+        d = torch.zeros((), dtype=torch.float64, device="cuda")
+        nxt = torch.zeros_like(lam)
+        kp.kp_scd_step(prob, lam, nxt, R=R, dual_sum=d)
+        outs.append((R.cpu().numpy().tobytes(), float(d), nxt.cpu().numpy().tobytes()))
+    assert outs[0] == outs[1]
+
+
+def test_graph_replay_matches_eager():
+    from paper_2002_00352_gb300.solver import ScdGraph, scd_solve
+    inst = gen.sparse_csr(N=20_000, device="cuda")
+    prob = _problem(inst)
+    lam0 = torch.zeros(inst.K, dtype=torch.float64, device="cuda")
+    eager, _ = scd_solve(prob, lam0, 6)
+    g = ScdGraph(prob, lam0)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(g.lam, eager)
