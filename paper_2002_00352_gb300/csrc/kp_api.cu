@@ -145,6 +145,7 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
         int l = order[t];
         int c = d->C[l];
         P.tree.cap[t] = (uint8_t)(c > 255 ? 255 : c);
+        P.tree.items[t] = d->S[l];
         for (int j = 0; j < d->M; ++j)
             if ((d->S[l] >> j) & 1ull) P.tree.ipath[j] |= 1u << t;
     }
@@ -152,7 +153,7 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
     kp_status st = KP_OK;
     // device scan of the instance (Sec. 2 data assumptions)
     uint32_t *flags = nullptr;
-    if ((st = alloc(h, &flags, 2, "validation flags")) != KP_OK) goto fail_out;
+    if ((st = alloc(h, &flags, 3, "validation flags")) != KP_OK) goto fail_out;
     {
         cudaError_t e = kp::launch_validate(P, flags, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -160,7 +161,7 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
             st = cuda_fail(e, "validate");
             goto fail_out;
         }
-        uint32_t hf[2] = {0, 0};
+        uint32_t hf[3] = {0, 0, 0};
         e = cudaMemcpy(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
             st = cuda_fail(e, "validate copy");
@@ -196,6 +197,14 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
         if (s > 40) s = 40;
         if (s < 4) s = 4;
         P.fixs = s;
+        // objective sums: every per-user value is below M * max p
+        float maxp;
+        memcpy(&maxp, &hf[2], 4);
+        double bo = (double)P.N * P.M * (double)maxp + 1.0;
+        int so = (int)std::floor(62.0 - std::log2(bo));
+        if (so > 40) so = 40;
+        if (so < 0) so = 0;
+        P.fixo = so;
     }
     {
         kp::Scratch &S = h->S;
@@ -204,26 +213,34 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
         double budget = env ? atof(env) : 4.0 * (double)P.N * P.M;
         if (!env) {
             if (budget < (double)(1 << 20)) budget = (double)(1 << 20);
-            if (budget > (double)(1 << 27)) budget = (double)(1 << 27);
+            if (budget > (double)(1 << 28)) budget = (double)(1 << 28);
         }
         long long cap = (long long)(budget / ((double)P.K * S.G));
         if (cap < 64) cap = 64;
         S.cap_kb = (int)cap;
         const size_t K = (size_t)P.K, G = (size_t)S.G;
         if ((st = alloc(h, &S.Rfix, K, "Rfix")) != KP_OK) goto fail_out;
-        if ((st = alloc(h, &S.dual_part, G, "dual partials")) != KP_OK) goto fail_out;
-        if ((st = alloc(h, &S.primal_part, G, "primal partials")) != KP_OK) goto fail_out;
-        if ((st = alloc(h, &S.hist, K * kp::NB, "histogram")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.objfix, 2, "objective sums")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.reg3, K * 3, "window masses")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.subhist, K * kp::NSUB, "sub-histogram")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.buf, K * G * (size_t)S.cap_kb, "breakpoint buffer")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.bufcnt, K * G, "buffer counts")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.ovf, K, "overflow flags")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.sel, K, "selection state")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.ctr, 1, "counters")) != KP_OK) goto fail_out;
+        if (P.layout == KP_B_CSR) {
+            if ((st = alloc(h, &S.shmask, (size_t)P.N, "shared-entry masks")) != KP_OK) goto fail_out;
+            cudaError_t e2 = kp::launch_shmask(P, S.shmask, 0);
+            if (e2 == cudaSuccess) e2 = cudaDeviceSynchronize();
+            if (e2 != cudaSuccess) {
+                st = cuda_fail(e2, "shared-entry masks");
+                goto fail_out;
+            }
+        }
         std::vector<kp::SelK> init(K);
         for (auto &x : init) {
             memset(&x, 0, sizeof(x));
-            x.w = kp::WMIN;
+            x.w = kp::WMIN_BITS;
         }
         cudaError_t e = cudaMemcpy(S.sel, init.data(), K * sizeof(kp::SelK), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {

@@ -171,16 +171,18 @@ __device__ __forceinline__ uint32_t key_of(float v) {
     return k > 0x7F7FFFFFu ? 0x7F7FFFFFu : k;
 }
 
-__device__ __forceinline__ int bucket_of(uint32_t key, uint32_t ckey) {
-    long long d = (long long)key - (long long)ckey;
-    if (d == 0) return NB_CENTRE;
-    unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
-    int e = 63 - __clzll((long long)ad);
-    return d > 0 ? NB_CENTRE + 1 + e : NB_CENTRE - 1 - e;
-}
-
-__device__ __forceinline__ unsigned long long fixmass(float v, float scale) {
-    return __float2ull_rn(v * scale);
+// round(v * 2^s) for finite v >= 0, with integer operations only (on GB300
+// the FP64 pipe, which also converts floats to 64-bit integers, is narrow).
+// Halves round up.  s is chosen at creation so that no sum can overflow.
+__device__ __forceinline__ unsigned long long fixmass(float v, int s) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)(b >> 23) & 0xff;
+    const uint32_t m = e ? ((b & 0x7fffffu) | 0x800000u) : (b & 0x7fffffu);
+    const int sh = (e ? e : 1) - 150 + s;  // v = m * 2^((e ? e : 1) - 150)
+    if (sh >= 0) return (unsigned long long)m << (sh > 39 ? 39 : sh);
+    const int r = -sh;
+    if (r > 25) return 0ull;
+    return (unsigned long long)((m + (1u << (r - 1))) >> r);
 }
 
 // ---------------------------------------------------------------------------
@@ -301,55 +303,74 @@ __device__ void sweep_k(const float *pt, int ps, const float *s, int ss, int M, 
 }
 
 // ---------------------------------------------------------------------------
+// shared-memory atomics through the shared state space (never generic)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void shared_add_u64(unsigned long long *p, unsigned long long v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t shared_inc_u32(uint32_t *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    uint32_t old;
+    asm volatile("atom.shared.add.u32 %0, [%1], 1;" : "=r"(old) : "r"(a) : "memory");
+    return old;
+}
+
+// ---------------------------------------------------------------------------
 // emission sinks
 // ---------------------------------------------------------------------------
-// First pass: log histogram around the centre + buffered window.
-struct HistSink {
-    unsigned long long *hist;  // [K][NB] (shared or global memory)
-    const uint32_t *ckey;      // [K]
-    const int32_t *wwin;       // [K]
-    uint32_t *bcnt;            // [K] buffer fill of this block
+// First pass: exact masses above / inside / below the window, and the
+// breakpoints inside the window buffered.
+struct WindowSink {
+    unsigned long long *reg3;  // [K][3] (shared)
+    const float4 *kinfo;       // [K] (shared): lambda_k (f32), window low, window high (exclusive)
+    uint32_t *bcnt;            // [K] buffer fill of this block (shared)
     uint2 *buf;
     int cap_kb, G, blk;
-    float scale;
-    __device__ __forceinline__ void emit(int k, float v1, float v2) {
-        if (!(v1 > 0.f) || !(v2 > 0.f)) return;
-        uint32_t key = key_of(v1);
-        int b = bucket_of(key, ckey[k]);
-        atomicAdd(&hist[(size_t)k * NB + b], fixmass(v2, scale));
-        int off = b - NB_CENTRE;
-        if (off < 0) off = -off;
-        if (off <= wwin[k]) {
-            uint32_t slot = atomicAdd(&bcnt[k], 1u);
+    int fixs;
+    __device__ __forceinline__ void emit_ki(int k, const float4 &ki, float v1, float v2) {
+        if (!(v1 > 0.f)) return;
+        const unsigned long long m = fixmass(v2, fixs);
+        const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
+        shared_add_u64(&reg3[3 * k + r], m);
+        if (r == 1) {
+            const uint32_t slot = shared_inc_u32(&bcnt[k]);
             if (slot < (uint32_t)cap_kb)
-                buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key, __float_as_uint(v2));
+                buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key_of(v1), __float_as_uint(v2));
         }
+    }
+    __device__ __forceinline__ void emit(int k, float v1, float v2) {
+        if (!(v2 > 0.f)) return;
+        emit_ki(k, kinfo[k], v1, v2);
     }
 };
 
 // Refine pass: sub-histogram of the unresolved range + buffer of its entries.
 struct RefineSink {
-    const uint32_t *lo, *hi;   // [K]; empty range for resolved knapsacks
-    const int32_t *shift;      // [K]
+    const uint32_t *lo, *hi;      // [K]; empty range for resolved knapsacks
+    const int32_t *shift;         // [K]
     unsigned long long *subhist;  // [K][NSUB] global
-    uint32_t *bcnt;
+    uint32_t *bcnt;               // [K] (shared)
     uint2 *buf;
     int cap_kb, G, blk;
-    float scale;
+    int fixs;
     __device__ __forceinline__ void emit(int k, float v1, float v2) {
         if (!(v1 > 0.f) || !(v2 > 0.f)) return;
-        uint32_t key = key_of(v1);
+        const uint32_t key = key_of(v1);
         if (key < lo[k] || key >= hi[k]) return;
-        int sb = (int)((key - lo[k]) >> shift[k]);
-        atomicAdd(&subhist[(size_t)k * NSUB + sb], fixmass(v2, scale));
-        uint32_t slot = atomicAdd(&bcnt[k], 1u);
+        const int sb = (int)((key - lo[k]) >> shift[k]);
+        atomicAdd(&subhist[(size_t)k * NSUB + sb], fixmass(v2, fixs));
+        const uint32_t slot = shared_inc_u32(&bcnt[k]);
         if (slot < (uint32_t)cap_kb)
             buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key, __float_as_uint(v2));
     }
+    __device__ __forceinline__ void emit_ki(int k, const float4 &, float v1, float v2) { emit(k, v1, v2); }
 };
 
 struct NullSink {
     __device__ __forceinline__ void emit(int, float, float) {}
+    __device__ __forceinline__ void emit_ki(int, const float4 &, float, float) {}
 };
 
 }  // namespace kp

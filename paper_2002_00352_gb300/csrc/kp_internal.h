@@ -8,29 +8,35 @@
 
 namespace kp {
 
-// Buckets of the per-knapsack breakpoint histogram built in the user pass.
-// Sec. 5.2 buckets candidate lambda_k values by the logarithm of their
-// distance from lambda_k^t.  Here the distance is measured in FP32 ulps
-// (the bit patterns of positive floats are ordered like their values):
-//   d = key(v1) - key(centre),  bucket = 32 + sign(d) (1 + floor(log2 |d|)),
-// and bucket 32 holds d = 0.  64 buckets cover every positive float.
-constexpr int NB = 64;
-constexpr int NB_CENTRE = 32;
+// Threshold selection (Reduce of Algorithm 4).  The breakpoint pass splits
+// every knapsack's breakpoints into three key ranges around a predicted
+// threshold (Sec. 5.2 centres its buckets at lambda_k^t for the same reason):
+// above the window, inside it and below it.  The masses of the three ranges
+// are accumulated exactly (64-bit fixed point) and the breakpoints inside the
+// window are buffered, so when the crossing falls inside the window the exact
+// breakpoint is selected from the buffer; otherwise the pass is re-run over the
+// range that holds the crossing with a 256-way sub-histogram.  Keys are the
+// FP32 bit patterns of the breakpoints, ordered like their values.
+constexpr uint32_t KEY_INF = 0x7F800000u;
 // sub-buckets used when a pass is re-run to narrow a key range
 constexpr int NSUB = 256;
 // re-run rounds of the user pass allowed inside one threshold selection
 constexpr int MAX_REFINE = 4;
-// smallest half-width (in buckets) of the buffered window around the centre
-constexpr int WMIN = 12;
+// smallest half-width of the window, in keys (2^12 ulps ~ 0.05 %)
+constexpr int WMIN_BITS = 12;
 
 // per-knapsack state of the threshold selection (device resident)
 struct SelK {
-    uint32_t ckey;        // key of the bucket centre used by the last pass
-    int32_t w;            // half-width of the buffered window for the next pass
+    uint32_t ckey;        // centre key used by the last pass
+    int32_t w;            // window half-width of the next pass: 2^w keys
+    uint32_t wlo, whi;    // window [wlo, whi) used by the last pass
     uint32_t lo, hi;      // unresolved key range [lo, hi)
-    unsigned long long above;  // fixed-point mass strictly above hi
+    unsigned long long above;  // fixed-point mass at or above hi
     int32_t state;        // 0 resolved, 1 needs a refine pass
     uint32_t last_nz_key; // key of the last non-zero lambda_k (centre when lambda_k = 0)
+    uint32_t for_key;     // key of the lambda_k the prediction below is for
+    uint32_t pred_key;    // predicted key of the next lambda_k (centre of the next pass)
+    uint32_t prev_key;    // key of the lambda_k before for_key
 };
 
 // global counters (device resident)
@@ -44,8 +50,9 @@ struct Counters {
 // (subsets first), so the lowest set bit of (path & mask) is the deepest node
 struct Tree {
     int32_t L;
-    uint32_t ipath[KP_MAX_M];  // bit l set iff item j belongs to node l
-    uint8_t cap[KP_MAX_L];     // C_l clamped to 255
+    uint32_t ipath[KP_MAX_M];     // bit l set iff item j belongs to node l
+    uint64_t items[KP_MAX_L];     // items of node l
+    uint8_t cap[KP_MAX_L];        // C_l clamped to 255
 };
 
 struct Params {
@@ -58,7 +65,8 @@ struct Params {
     const float *val;
     const int16_t *kidx;
     const double *B;
-    int32_t fixs;              // fixed-point shift: mass units of 2^-fixs
+    int32_t fixs;              // fixed-point shift of b sums: units of 2^-fixs
+    int32_t fixo;              // fixed-point shift of the objective sums
     Tree tree;
 };
 
@@ -67,14 +75,15 @@ struct Scratch {
     int32_t G;                        // persistent grid size of the user pass
     int32_t cap_kb;                   // buffer entries per (k, block)
     unsigned long long *Rfix;         // [K]
-    double *dual_part, *primal_part;  // [G]
-    unsigned long long *hist;         // [K][NB]
+    unsigned long long *objfix;       // [2] fixed-point dual and primal sums
+    unsigned long long *reg3;         // [K][3] mass at/above, inside, below the window
     unsigned long long *subhist;      // [K][NSUB]
     uint2 *buf;                       // [K][G][cap_kb] (key, float bits of v2)
     uint32_t *bufcnt;                 // [K][G]
     uint32_t *ovf;                    // [K]
     SelK *sel;                        // [K]
     Counters *ctr;
+    uint32_t *shmask;                 // [N] CSR: entries whose knapsack another item of the user also uses
 };
 
 enum PassMode { MODE_STATE = 0, MODE_HIST = 1, MODE_REFINE = 2 };
@@ -97,5 +106,6 @@ cudaError_t launch_backward(const Params &P, const double *lambda, const uint32_
                             const double *R, const double *upstream, double *grad_lambda,
                             float *grad_p, double *grad_B, cudaStream_t st);
 cudaError_t launch_validate(const Params &P, uint32_t *flags, cudaStream_t st);
+cudaError_t launch_shmask(const Params &P, uint32_t *shmask, cudaStream_t st);
 
 }  // namespace kp

@@ -7,9 +7,10 @@
 //                consumption R_k = sum_i v_ik (Algorithm 2), dual and primal
 //                sums.
 //   MODE_HIST    MODE_STATE + Algorithm 4's Map: every user's breakpoints of
-//                its k-consumption, aggregated into per-knapsack histograms
-//                bucketed around lambda_k^t (Sec. 5.2) plus a buffered window
-//                of exact breakpoints around the centre.
+//                its k-consumption, aggregated per knapsack into the exact
+//                masses above / inside / below a window around the predicted
+//                threshold (Sec. 5.2 centres its buckets at lambda_k^t), with
+//                the breakpoints inside the window buffered.
 //   MODE_REFINE  Algorithm 4's Map restricted to the key ranges still
 //                unresolved by the threshold selection.
 //
@@ -27,12 +28,10 @@ namespace kp {
 
 namespace {
 
-constexpr int HIST_SMEM_BYTES = 112 * 1024;   // per-block histogram kept in shared memory if it fits
 constexpr int DENSE_TILE_BYTES = 64 * 1024;   // dense b tile
 
 struct SmemLayout {
-    size_t lamf, ckey, wwin, bcnt, lo, hi, shift, rfix, hist, rows, tile_p, tile_b, selm, red, total;
-    bool hist_in_smem;
+    size_t lamf, kinfo, ckey, wwin, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -43,6 +42,8 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     size_t o = 0;
     s.lamf = o;
     o = align16(o + 4 * (size_t)K);
+    s.kinfo = o;
+    o = align16(o + 16 * (size_t)K);
     s.ckey = o;
     o = align16(o + 4 * (size_t)K);
     s.wwin = o;
@@ -57,14 +58,13 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     o = align16(o + 4 * (size_t)K);
     s.rfix = o;
     o = align16(o + 8 * (size_t)K);
-    s.hist_in_smem = (mode == MODE_HIST) && ((size_t)K * NB * 8 <= (size_t)HIST_SMEM_BYTES);
-    s.hist = o;
-    if (s.hist_in_smem) o = align16(o + (size_t)K * NB * 8);
+    s.reg3 = o;
+    if (mode == MODE_HIST) o = align16(o + (size_t)K * 3 * 8);
     s.red = o;
     o = align16(o + 2 * 8 * 32);
     if (layout == KP_B_CSR) {
-        s.rows = o;
-        o = align16(o + 2 * 4 * (size_t)threads * maxm);
+        s.rows = o;  // p~ rows of users with shared-knapsack sweeps
+        if (mode != MODE_STATE) o = align16(o + 4 * (size_t)threads * maxm);
         s.tile_p = s.tile_b = s.selm = o;
     } else {
         s.tile_p = o;
@@ -102,10 +102,30 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
         rfix[k] = 0;
         if (MODE == MODE_HIST) {
             SelK sk = S.sel[k];
-            uint32_t c = lf > 0.f ? __float_as_uint(lf) : sk.last_nz_key;
+            const uint32_t lk = lf > 0.f ? __float_as_uint(lf) : 0u;
+            uint32_t c;
+            if (sk.pred_key && sk.for_key == lk)  // continuing the trajectory the select predicted
+                c = sk.pred_key;
+            else
+                c = lk ? lk : sk.last_nz_key;
+            const long long H = 1ll << sk.w;
+            const long long wl = (long long)c - H, wh = (long long)c + H + 1;
+            const uint32_t wlo = wl < 1 ? 1u : (uint32_t)wl;
+            const uint32_t whi = wh > (long long)KEY_INF ? KEY_INF : (uint32_t)wh;
             ckey[k] = c;
             wwin[k] = sk.w;
-            if (blockIdx.x == 0) S.sel[k].ckey = c;
+            if (blockIdx.x == 0) {
+                S.sel[k].ckey = c;
+                S.sel[k].wlo = wlo;
+                S.sel[k].whi = whi;
+            }
+            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, __uint_as_float(wlo), __uint_as_float(whi), 0.f);
+            unsigned long long *r3 = (unsigned long long *)(smem + L.reg3);
+            r3[3 * k] = 0ull;
+            r3[3 * k + 1] = 0ull;
+            r3[3 * k + 2] = 0ull;
+        } else {
+            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, 0.f, 0.f, 0.f);
         }
         if (MODE == MODE_REFINE) {
             SelK sk = S.sel[k];
@@ -122,20 +142,15 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
             }
         }
     }
-    if (MODE == MODE_HIST && L.hist_in_smem) {
-        unsigned long long *h = (unsigned long long *)(smem + L.hist);
-        for (int q = threadIdx.x; q < K * NB; q += blockDim.x) h[q] = 0ull;
-    }
 }
 
 template <int MODE>
 __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch &S,
                                                   const SmemLayout &L, unsigned char *smem,
-                                                  double dsum, double psum) {
+                                                  unsigned long long dsum, unsigned long long psum) {
     const int K = P.K;
     uint32_t *bcnt = (uint32_t *)(smem + L.bcnt);
     unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
-    double *red = (double *)(smem + L.red);
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         if (MODE != MODE_REFINE && rfix[k]) atomicAdd(&S.Rfix[k], rfix[k]);
@@ -145,184 +160,539 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
             if (c > (uint32_t)S.cap_kb) S.ovf[k] = 1u;
         }
     }
-    if (MODE == MODE_HIST && L.hist_in_smem) {
-        unsigned long long *h = (unsigned long long *)(smem + L.hist);
-        for (int q = threadIdx.x; q < K * NB; q += blockDim.x)
-            if (h[q]) atomicAdd(&S.hist[q], h[q]);
+    if (MODE == MODE_HIST) {
+        unsigned long long *r3 = (unsigned long long *)(smem + L.reg3);
+        for (int q = threadIdx.x; q < K * 3; q += blockDim.x)
+            if (r3[q]) atomicAdd(&S.reg3[q], r3[q]);
     }
     if (MODE != MODE_REFINE) {
-        // block reduction of the FP64 objective sums in a fixed order
+        // exact fixed-point objective sums: warp reduction, one atomic per warp
         for (int o = 16; o > 0; o >>= 1) {
             dsum += __shfl_down_sync(0xffffffffu, dsum, o);
             psum += __shfl_down_sync(0xffffffffu, psum, o);
         }
-        int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (lane == 0) {
-            red[wid] = dsum;
-            red[32 + wid] = psum;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-                a += red[q];
-                b += red[32 + q];
-            }
-            S.dual_part[blockIdx.x] = a;
-            S.primal_part[blockIdx.x] = b;
+        if ((threadIdx.x & 31) == 0) {
+            if (dsum) atomicAdd(&S.objfix[0], dsum);
+            if (psum) atomicAdd(&S.objfix[1], psum);
         }
     }
 }
 
+__device__ __forceinline__ WindowSink make_window_sink(const Params &P, const Scratch &S,
+                                                       const SmemLayout &L, unsigned char *smem) {
+    WindowSink ws;
+    ws.reg3 = (unsigned long long *)(smem + L.reg3);
+    ws.kinfo = (const float4 *)(smem + L.kinfo);
+    ws.bcnt = (uint32_t *)(smem + L.bcnt);
+    ws.buf = S.buf;
+    ws.cap_kb = S.cap_kb;
+    ws.G = S.G;
+    ws.blk = blockIdx.x;
+    ws.fixs = P.fixs;
+    return ws;
+}
+
+__device__ __forceinline__ RefineSink make_refine_sink(const Params &P, const Scratch &S,
+                                                       const SmemLayout &L, unsigned char *smem) {
+    RefineSink rs;
+    rs.lo = (const uint32_t *)(smem + L.lo);
+    rs.hi = (const uint32_t *)(smem + L.hi);
+    rs.shift = (const int32_t *)(smem + L.shift);
+    rs.subhist = S.subhist;
+    rs.bcnt = (uint32_t *)(smem + L.bcnt);
+    rs.buf = S.buf;
+    rs.cap_kb = S.cap_kb;
+    rs.G = S.G;
+    rs.blk = blockIdx.x;
+    rs.fixs = P.fixs;
+    return rs;
+}
+
 // ------------------------------------------------------------------------------------------
-// CSR layout: one thread per user.
+// CSR layout: one thread per user, users in tiles of THREADS consecutive users.
+// The entry offsets of a tile come from one csr_user_off read plus a block scan
+// of the users' entry counts (csr_user_off is consistent with csr_item_nnz,
+// checked at creation).  Entries whose knapsack is also consumed by another
+// item of the same user are marked once at creation (Scratch::shmask); all
+// other entries get the closed-form breakpoint in one uniform loop, and the
+// few shared knapsacks run the kinetic sweep afterwards.
 // ------------------------------------------------------------------------------------------
+template <int THREADS>
+__device__ __forceinline__ int block_excl_scan(int v, int *s_scan) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_scan[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < THREADS / 32 ? s_scan[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < THREADS / 32) s_scan[lane] = t;
+    }
+    __syncthreads();
+    return (wid > 0 ? s_scan[wid - 1] : 0) + x - v;
+}
+
 template <int MAXM, int MODE, class Sink>
-__device__ __forceinline__ void csr_user(const Params &P, int64_t i, const float *lamf, float *pt,
-                                         float *th, unsigned long long *rfix, double &dsum,
-                                         double &psum, uint32_t *x_bits, Sink &sink) {
+__device__ __forceinline__ void csr_user(const Params &P, const Scratch &S, int64_t i, int64_t e0,
+                                         int nnz, const float *lamf, float *pt, float *mg,
+                                         unsigned long long *rfix, unsigned long long &dsum, unsigned long long &psum,
+                                         uint32_t *x_bits, Sink &sink) {
     const int M = P.M;
     const Tree &T = P.tree;
     const float *pr = P.p + (size_t)i * M;
     const uint8_t *nzr = P.innz + (size_t)i * M;
-    const int64_t e0 = P.uoff[i];
-    const float *val = P.val;
-    const int16_t *kid = P.kidx;
+    const float *val = P.val + e0;
+    const int16_t *kid = P.kidx + e0;
 
     // Sec. 4.2: p~_ij = p_ij - sum_k lambda_k b_ijk over the item's entries
     uint64_t pos = 0;
-    int64_t e = e0;
-    for (int j = 0; j < M; ++j) {
-        float acc = __ldg(pr + j);
-        int c = nzr[j];
-        for (int q = 0; q < c; ++q, ++e) acc = fmaf(-lamf[kid[e]], __ldg(val + e), acc);
-        pt[j] = acc;
-        if (acc > 0.f) pos |= 1ull << j;
+    {
+        int e = 0;
+        for (int j = 0; j < M; ++j) {
+            float acc = __ldg(pr + j);
+            const int c = nzr[j];
+            for (int q = 0; q < c; ++q, ++e) acc = fmaf(-lamf[kid[e]], __ldg(val + e), acc);
+            pt[j] = acc;
+            if (acc > 0.f) pos |= 1ull << j;
+        }
     }
     // Algorithm 1
     Walk w;
     greedy_walk(pt, 1, pos, T, w);
 
     if (MODE != MODE_REFINE) {
-        if (x_bits) {
+        if (x_bits)
             for (int q = 0; q < P.W; ++q) x_bits[(size_t)i * P.W + q] = (uint32_t)(w.sel >> (32 * q));
-        }
-        float scale = __uint_as_float((uint32_t)(127 + P.fixs) << 23);
-        e = e0;
+        int e = 0;
+        float du = 0.f, pu = 0.f;
         for (int j = 0; j < M; ++j) {
-            int c = nzr[j];
+            const int c = nzr[j];
             if ((w.sel >> j) & 1ull) {
-                dsum += (double)pt[j];
-                psum += (double)__ldg(pr + j);
+                du += pt[j];
+                pu += __ldg(pr + j);
                 for (int q = 0; q < c; ++q)
-                    atomicAdd(&rfix[kid[e + q]], fixmass(__ldg(val + e + q), scale));
+                    shared_add_u64(&rfix[kid[e + q]], fixmass(__ldg(val + e + q), P.fixs));
             }
             e += c;
         }
+        dsum += fixmass(du, P.fixo);
+        psum += fixmass(pu, P.fixo);
     }
-    if (MODE != MODE_STATE) {
-        item_thresholds(pt, M, w, T, th);
-        e = e0;
+    if (MODE == MODE_STATE) return;
+
+    // Algorithm 4 Map.  margin_j = p~_j - theta_j: with a single moving line the
+    // breakpoint is lambda_k + margin_j / b_jk.
+    item_thresholds(pt, M, w, T, mg);
+    for (int j = 0; j < M; ++j) mg[j] = pt[j] - mg[j];
+    uint32_t pending = 0;  // first entries of the knapsacks shared by several items
+    if (nnz <= 32) {
+        const uint32_t shm = S.shmask[i];
+        int e = 0;
         for (int j = 0; j < M; ++j) {
-            int c = nzr[j];
-            for (int q = 0; q < c; ++q) {
-                const int64_t idx = e + q;
-                const float v = __ldg(val + idx);
+            const int c = nzr[j];
+            const float m = mg[j];
+            for (int q = 0; q < c; ++q, ++e) {
+                if ((shm >> e) & 1u) {
+                    const int k = kid[e];
+                    uint32_t earlier = shm & ((1u << e) - 1u);
+                    bool first = true;
+                    while (earlier) {
+                        const int f = __ffs(earlier) - 1;
+                        earlier &= earlier - 1;
+                        if (kid[f] == k) first = false;
+                    }
+                    if (first) pending |= 1u << e;
+                    continue;
+                }
+                const float v = __ldg(val + e);
                 if (!(v > 0.f)) continue;
-                const int k = kid[idx];
-                // does another item of this user also consume knapsack k?
+                const int k = kid[e];
+                sink.emit(k, lamf[k] + __fdividef(m, v), v);
+            }
+        }
+    } else {
+        // long rows: find shared knapsacks by scanning (no precomputed mask)
+        int e = 0;
+        for (int j = 0; j < M; ++j) {
+            const int c = nzr[j];
+            for (int q = 0; q < c; ++q, ++e) {
+                const float v = __ldg(val + e);
+                if (!(v > 0.f)) continue;
+                const int k = kid[e];
                 bool shared = false, first = true;
-                int64_t f = e0;
+                int f = 0;
                 for (int j2 = 0; j2 < M; ++j2) {
-                    int c2 = nzr[j2];
-                    if (j2 != j) {
+                    const int c2 = nzr[j2];
+                    if (j2 != j)
                         for (int q2 = 0; q2 < c2; ++q2)
                             if (kid[f + q2] == k && __ldg(val + f + q2) > 0.f) {
                                 shared = true;
-                                if (f + q2 < idx) first = false;
+                                if (f + q2 < e) first = false;
                             }
-                    }
                     f += c2;
                 }
                 if (!shared) {
-                    // single moving line: it is selected iff p~_j(lambda_k) > theta_j
-                    float v1 = lamf[k] + (pt[j] - th[j]) / v;
-                    sink.emit(k, v1, v);
+                    sink.emit(k, lamf[k] + __fdividef(mg[j], v), v);
                 } else if (first) {
                     float s[MAXM];
                     uint64_t J = 0;
-                    int64_t f2 = e0;
+                    int f2 = 0;
                     for (int j2 = 0; j2 < M; ++j2) {
-                        int c2 = nzr[j2];
+                        const int c2 = nzr[j2];
                         s[j2] = 0.f;
-                        for (int q2 = 0; q2 < c2; ++q2)
-                            if (kid[f2 + q2] == k) {
-                                float vv = __ldg(val + f2 + q2);
+                        for (int q2 = 0; q2 < c2; ++q2, ++f2)
+                            if (kid[f2] == k) {
+                                const float vv = __ldg(val + f2);
                                 if (vv > 0.f) {
                                     s[j2] = vv;
                                     J |= 1ull << j2;
                                 }
                             }
-                        f2 += c2;
                     }
                     sweep_k<MAXM>(pt, 1, s, 1, M, J, lamf[k], T, k, sink);
                 }
             }
-            e += c;
         }
+    }
+    // shared knapsacks: the kinetic sweep, batched after the uniform loop
+    while (pending) {
+        const int e = __ffs(pending) - 1;
+        pending &= pending - 1;
+        const int k = kid[e];
+        float s[MAXM];
+        uint64_t J = 0;
+        int f = 0;
+        for (int j2 = 0; j2 < M; ++j2) {
+            const int c2 = nzr[j2];
+            s[j2] = 0.f;
+            for (int q2 = 0; q2 < c2; ++q2, ++f)
+                if (kid[f] == k) {
+                    const float vv = __ldg(val + f);
+                    if (vv > 0.f) {
+                        s[j2] = vv;
+                        J |= 1ull << j2;
+                    }
+                }
+        }
+        sweep_k<MAXM>(pt, 1, s, 1, M, J, lamf[k], T, k, sink);
+    }
+}
+
+// Lean per-user routine for M <= MAXM <= 16 and at most 32 entries: reduced
+// costs, decisions and margins live in registers, loops run over the items in
+// compile-time order with predication, so the lanes of a warp stay together.
+//   Algorithm 1 is evaluated in its literal bottom-up form: beats[j] is the set
+//   of items ranked before j (larger p~, ties to the lower index); at set S_l
+//   an item survives if fewer than C_l survivors of S_l rank before it.
+template <int MAXM, int MODE, class Sink>
+__device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch &S, int64_t i,
+                                                  int64_t e0, const float4 *kinfo,
+                                                  unsigned long long *rfix, unsigned long long &dsum,
+                                                  unsigned long long &psum, uint32_t *x_bits,
+                                                  Sink &sink, float *prow) {
+    const int M = P.M;
+    const Tree &T = P.tree;
+    const float *pr = P.p + (size_t)i * M;
+    const uint8_t *nzr = P.innz + (size_t)i * M;
+    const float *val = P.val + e0;
+    const int16_t *kid = P.kidx + e0;
+
+    float pt[MAXM];
+    int cnt[MAXM];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+        pt[j] = j < M ? __ldg(pr + j) : 0.f;
+        cnt[j] = j < M ? (int)nzr[j] : 0;
+    }
+    // Sec. 4.2 reduced costs
+    {
+        int e = 0;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+            float acc = pt[j];
+            for (int q = 0; q < cnt[j]; ++q, ++e) acc = fmaf(-kinfo[kid[e]].x, __ldg(val + e), acc);
+            pt[j] = acc;
+        }
+    }
+    // Algorithm 1
+    uint32_t beats[MAXM];
+    uint32_t pos = 0;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+        beats[j] = 0u;
+        if (j < M && pt[j] > 0.f) pos |= 1u << j;
+    }
+#pragma unroll
+    for (int j = 1; j < MAXM; ++j)
+#pragma unroll
+        for (int j2 = 0; j2 < j; ++j2) {
+            const bool first = pt[j2] >= pt[j];  // j2 < j wins ties
+            beats[j] |= first ? (1u << j2) : 0u;
+            beats[j2] |= first ? 0u : (1u << j);
+        }
+    uint32_t G = pos;
+    for (int l = 0; l < T.L; ++l) {
+        const uint32_t inl = G & (uint32_t)T.items[l];
+        const int cap = T.cap[l];
+        uint32_t drop = 0u;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+            if (((inl >> j) & 1u) && __popc(beats[j] & inl) >= cap) drop |= 1u << j;
+        G &= ~drop;
+    }
+    uint32_t full = 0u;
+    for (int l = 0; l < T.L; ++l)
+        if (__popc(G & (uint32_t)T.items[l]) >= (int)T.cap[l]) full |= 1u << l;
+
+    if (MODE != MODE_REFINE) {
+        if (x_bits) x_bits[(size_t)i * P.W] = G;
+        int e = 0;
+        float du = 0.f, pu = 0.f;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+            if ((G >> j) & 1u) {
+                du += pt[j];
+                pu += __ldg(pr + j);
+                for (int q = 0; q < cnt[j]; ++q)
+                    shared_add_u64(&rfix[kid[e + q]], fixmass(__ldg(val + e + q), P.fixs));
+            }
+            e += cnt[j];
+        }
+        dsum += fixmass(du, P.fixo);
+        psum += fixmass(pu, P.fixo);
+    }
+    if (MODE == MODE_STATE) return 0u;
+
+    // exchange thresholds theta_j and margins p~_j - theta_j
+    float minSel[KP_MAX_L], maxCut[KP_MAX_L];
+    for (int l = 0; l < T.L; ++l) {
+        minSel[l] = FLT_MAX;
+        maxCut[l] = 0.f;
+    }
+    const uint32_t rej = pos & ~G;
+#pragma unroll
+    for (int y = 0; y < MAXM; ++y) {
+        if (y < M) {
+            uint32_t path = T.ipath[y];
+            if ((G >> y) & 1u) {
+                while (path) {
+                    const int l = __ffs(path) - 1;
+                    path &= path - 1;
+                    minSel[l] = fminf(minSel[l], pt[y]);
+                }
+            } else if ((rej >> y) & 1u) {
+                const uint32_t f = path & full;
+                if (f) {
+                    const int l = __ffs(f) - 1;
+                    maxCut[l] = fmaxf(maxCut[l], pt[y]);
+                }
+            }
+        }
+    }
+    float mg[MAXM];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+        float th = 0.f;
+        if (j < M) {
+            uint32_t path = T.ipath[j];
+            if ((G >> j) & 1u) {
+                while (path) {
+                    const int l = __ffs(path) - 1;
+                    path &= path - 1;
+                    th = fmaxf(th, maxCut[l]);
+                }
+            } else {
+                const uint32_t f = path & full;
+                if (f) th = minSel[__ffs(f) - 1];
+            }
+        }
+        mg[j] = pt[j] - th;
+    }
+    // Algorithm 4 Map: closed form for knapsacks only one item touches
+    const uint32_t shm = S.shmask[i];
+    uint32_t pending = 0u;
+    {
+        int e = 0;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+            for (int q = 0; q < cnt[j]; ++q, ++e) {
+                const int k = kid[e];
+                if ((shm >> e) & 1u) {
+                    uint32_t earlier = shm & ((1u << e) - 1u);
+                    bool firstk = true;
+                    while (earlier) {
+                        const int f = __ffs(earlier) - 1;
+                        earlier &= earlier - 1;
+                        if (kid[f] == k) firstk = false;
+                    }
+                    if (firstk) pending |= 1u << e;
+                    continue;
+                }
+                const float v = __ldg(val + e);
+                if (v > 0.f) {
+                    const float4 ki = kinfo[k];
+                    sink.emit_ki(k, ki, ki.x + __fdividef(mg[j], v), v);
+                }
+            }
+        }
+    }
+    if (pending) {
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) prow[j] = pt[j];
+    }
+    return pending;
+}
+
+// One shared-knapsack sweep: the owner's p~ row is in shared memory, its
+// entries are read again to collect the slopes b_jk of knapsack k.
+template <int MAXM, class Sink>
+__device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo, const float *prow,
+                                           int64_t i, int64_t e0, int e, Sink &sink) {
+    const int M = P.M;
+    const uint8_t *nzr = P.innz + (size_t)i * M;
+    const float *val = P.val + e0;
+    const int16_t *kid = P.kidx + e0;
+    const int k = kid[e];
+    float sv[MAXM];
+    uint64_t J = 0;
+    int f = 0;
+    for (int j2 = 0; j2 < M; ++j2) {
+        const int c2 = nzr[j2];
+        sv[j2] = 0.f;
+        for (int q2 = 0; q2 < c2; ++q2, ++f)
+            if (kid[f] == k) {
+                const float vv = __ldg(val + f);
+                if (vv > 0.f) {
+                    sv[j2] = vv;
+                    J |= 1ull << j2;
+                }
+            }
+    }
+    sweep_k<MAXM>(prow, 1, sv, 1, M, J, kinfo[k].x, P.tree, k, sink);
+}
+
+// The sweeps of a warp's users are pooled and dealt round-robin to its lanes,
+// so that a user with several shared knapsacks does not keep 31 lanes idle.
+// Called by every lane of the warp.
+template <int MAXM, int THREADS, class Sink>
+__device__ __forceinline__ void warp_sweeps(const Params &P, const float4 *kinfo, float *rows,
+                                            int64_t i, int64_t e0, uint32_t pending, Sink &sink) {
+    constexpr int QCAP = 64;
+    __shared__ uint32_t q[THREADS / 32][QCAP];
+    __shared__ long long wi[THREADS], we0[THREADS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wbase = threadIdx.x & ~31;
+    const int n = __popc(pending);
+    int x = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, x, 31);
+    if (total == 0) return;
+    if (pending) {
+        wi[threadIdx.x] = i;
+        we0[threadIdx.x] = e0;
+    }
+    int slot = x - n;
+    uint32_t pm = pending;
+    while (pm) {
+        const int e = __ffs(pm) - 1;
+        pm &= pm - 1;
+        if (slot < QCAP) q[warp][slot] = ((uint32_t)lane << 5) | (uint32_t)e;
+        ++slot;
+    }
+    __syncwarp();
+    const int nq = total < QCAP ? total : QCAP;
+    for (int t = lane; t < nq; t += 32) {
+        const uint32_t d = q[warp][t];
+        const int owner = wbase + (int)(d >> 5);
+        sweep_task<MAXM>(P, kinfo, rows + (size_t)owner * MAXM, wi[owner], we0[owner], (int)(d & 31u), sink);
+    }
+    // tasks beyond the queue's capacity stay with their owners
+    slot = x - n;
+    pm = pending;
+    while (pm) {
+        const int e = __ffs(pm) - 1;
+        pm &= pm - 1;
+        if (slot >= QCAP) sweep_task<MAXM>(P, kinfo, rows + (size_t)threadIdx.x * MAXM, i, e0, e, sink);
+        ++slot;
+    }
+    __syncwarp();
+}
+
+template <int MAXM, int MODE, int THREADS, class Sink>
+__device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsigned char *smem,
+                                         const SmemLayout &L, uint32_t *x_bits, Sink &sink,
+                                         unsigned long long &dsum, unsigned long long &psum) {
+    __shared__ int s_scan[THREADS / 32];
+    __shared__ long long s_base;
+    const int M = P.M;
+    const float *lamf = (const float *)(smem + L.lamf);
+    const float4 *kinfo = (const float4 *)(smem + L.kinfo);
+    unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
+    for (int64_t base = (int64_t)blockIdx.x * THREADS; base < P.N; base += (int64_t)gridDim.x * THREADS) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < P.N;
+        if (threadIdx.x == 0) s_base = P.uoff[base];
+        int nnz = 0;
+        if (valid) {
+            const uint8_t *nzr = P.innz + (size_t)i * M;
+            for (int j = 0; j < M; ++j) nnz += nzr[j];
+        }
+        const int excl = block_excl_scan<THREADS>(nnz, s_scan);
+        const int64_t e0 = s_base + excl;
+        uint32_t pending = 0u;
+        float *rows = (float *)(smem + L.rows);
+        if (valid) {
+            bool done = false;
+            if constexpr (MAXM <= 16) {
+                if (nnz <= 32) {
+                    pending = csr_user_fast<MAXM, MODE>(P, S, i, e0, kinfo, rfix, dsum, psum, x_bits, sink,
+                                                        rows + (size_t)threadIdx.x * MAXM);
+                    done = true;
+                }
+            }
+            if (!done) {
+                float ptl[MAXM], mgl[MAXM];
+                csr_user<MAXM, MODE>(P, S, i, e0, nnz, lamf, ptl, mgl, rfix, dsum, psum, x_bits, sink);
+            }
+        }
+        if constexpr (MODE != MODE_STATE) {
+            if constexpr (MAXM <= 16) warp_sweeps<MAXM, THREADS>(P, kinfo, rows, i, e0, pending, sink);
+        }
+        __syncthreads();
     }
 }
 
 template <int MAXM, int MODE, int THREADS>
-__global__ void __launch_bounds__(THREADS) csr_pass_kernel(Params P, Scratch S, const double *lam,
-                                                           uint32_t *x_bits, int round) {
+__global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch S, const double *lam,
+                                                              uint32_t *x_bits, int round) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
     if (MODE != MODE_STATE && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&S.ctr->stats[0], 1ull);
     const SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, THREADS, 0, MODE);
     init_block_state<MODE>(P, S, lam, L, smem, round);
     __syncthreads();
-    const float *lamf = (const float *)(smem + L.lamf);
-    unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
-    float *pt = (float *)(smem + L.rows) + (size_t)threadIdx.x * MAXM;
-    float *th = (float *)(smem + L.rows) + (size_t)(THREADS + threadIdx.x) * MAXM;
-    double dsum = 0.0, psum = 0.0;
-
-    HistSink hs;
-    RefineSink rs;
+    unsigned long long dsum = 0ull, psum = 0ull;
     if (MODE == MODE_HIST) {
-        hs.hist = L.hist_in_smem ? (unsigned long long *)(smem + L.hist) : S.hist;
-        hs.ckey = (const uint32_t *)(smem + L.ckey);
-        hs.wwin = (const int32_t *)(smem + L.wwin);
-        hs.bcnt = (uint32_t *)(smem + L.bcnt);
-        hs.buf = S.buf;
-        hs.cap_kb = S.cap_kb;
-        hs.G = S.G;
-        hs.blk = blockIdx.x;
-        hs.scale = __uint_as_float((uint32_t)(127 + P.fixs) << 23);
-    }
-    if (MODE == MODE_REFINE) {
-        rs.lo = (const uint32_t *)(smem + L.lo);
-        rs.hi = (const uint32_t *)(smem + L.hi);
-        rs.shift = (const int32_t *)(smem + L.shift);
-        rs.subhist = S.subhist;
-        rs.bcnt = (uint32_t *)(smem + L.bcnt);
-        rs.buf = S.buf;
-        rs.cap_kb = S.cap_kb;
-        rs.G = S.G;
-        rs.blk = blockIdx.x;
-        rs.scale = __uint_as_float((uint32_t)(127 + P.fixs) << 23);
-    }
-    const int64_t stride = (int64_t)gridDim.x * THREADS;
-    for (int64_t i = (int64_t)blockIdx.x * THREADS + threadIdx.x; i < P.N; i += stride) {
-        if (MODE == MODE_HIST)
-            csr_user<MAXM, MODE>(P, i, lamf, pt, th, rfix, dsum, psum, x_bits, hs);
-        else if (MODE == MODE_REFINE)
-            csr_user<MAXM, MODE>(P, i, lamf, pt, th, rfix, dsum, psum, x_bits, rs);
-        else {
-            NullSink ns;
-            csr_user<MAXM, MODE>(P, i, lamf, pt, th, rfix, dsum, psum, x_bits, ns);
-        }
+        WindowSink ws = make_window_sink(P, S, L, smem);
+        csr_loop<MAXM, MODE, THREADS>(P, S, smem, L, x_bits, ws, dsum, psum);
+    } else if (MODE == MODE_REFINE) {
+        RefineSink rs = make_refine_sink(P, S, L, smem);
+        csr_loop<MAXM, MODE, THREADS>(P, S, smem, L, x_bits, rs, dsum, psum);
+    } else {
+        NullSink ns;
+        csr_loop<MAXM, MODE, THREADS>(P, S, smem, L, x_bits, ns, dsum, psum);
     }
     flush_block_state<MODE>(P, S, L, smem, dsum, psum);
 }
@@ -348,34 +718,8 @@ __global__ void __launch_bounds__(THREADS) dense_pass_kernel(Params P, Scratch S
     float *tb = (float *)(smem + L.tile_b);
     float *pt = (float *)(smem + L.rows);
     uint64_t *selm = (uint64_t *)(smem + L.selm);
-    const float scale = __uint_as_float((uint32_t)(127 + P.fixs) << 23);
-    double dsum = 0.0, psum = 0.0;
+    unsigned long long dsum = 0ull, psum = 0ull;
 
-    HistSink hs;
-    RefineSink rs;
-    if (MODE == MODE_HIST) {
-        hs.hist = L.hist_in_smem ? (unsigned long long *)(smem + L.hist) : S.hist;
-        hs.ckey = (const uint32_t *)(smem + L.ckey);
-        hs.wwin = (const int32_t *)(smem + L.wwin);
-        hs.bcnt = (uint32_t *)(smem + L.bcnt);
-        hs.buf = S.buf;
-        hs.cap_kb = S.cap_kb;
-        hs.G = S.G;
-        hs.blk = blockIdx.x;
-        hs.scale = scale;
-    }
-    if (MODE == MODE_REFINE) {
-        rs.lo = (const uint32_t *)(smem + L.lo);
-        rs.hi = (const uint32_t *)(smem + L.hi);
-        rs.shift = (const int32_t *)(smem + L.shift);
-        rs.subhist = S.subhist;
-        rs.bcnt = (uint32_t *)(smem + L.bcnt);
-        rs.buf = S.buf;
-        rs.cap_kb = S.cap_kb;
-        rs.G = S.G;
-        rs.blk = blockIdx.x;
-        rs.scale = scale;
-    }
     const bool b_al = ((reinterpret_cast<uintptr_t>(P.b) & 15u) == 0) && ((M * K) % 4 == 0 || T % 4 == 0);
     const bool p_al = ((reinterpret_cast<uintptr_t>(P.p) & 15u) == 0) && ((M % 4) == 0 || T % 4 == 0);
     const int64_t ntiles = (P.N + T - 1) / T;
@@ -437,12 +781,15 @@ __global__ void __launch_bounds__(THREADS) dense_pass_kernel(Params P, Scratch S
                 if (x_bits)
                     for (int q = 0; q < P.W; ++q) x_bits[(size_t)i * P.W + q] = (uint32_t)(w.sel >> (32 * q));
                 uint64_t r = w.sel;
+                float du = 0.f, pu = 0.f;
                 while (r) {
                     int j = __ffsll((long long)r) - 1;
                     r &= r - 1;
-                    dsum += (double)ptu[j];
-                    psum += (double)tp[(size_t)u * M + j];
+                    du += ptu[j];
+                    pu += tp[(size_t)u * M + j];
                 }
+                dsum += fixmass(du, P.fixo);
+                psum += fixmass(pu, P.fixo);
             }
         }
         __syncthreads();
@@ -456,18 +803,21 @@ __global__ void __launch_bounds__(THREADS) dense_pass_kernel(Params P, Scratch S
                 while (r) {
                     int j = __ffsll((long long)r) - 1;
                     r &= r - 1;
-                    acc += fixmass(bcol[(size_t)j * K], scale);
+                    acc += fixmass(bcol[(size_t)j * K], P.fixs);
                 }
-                if (acc) atomicAdd(&rfix[k], acc);
+                if (acc) shared_add_u64(&rfix[k], acc);
             }
             if (MODE != MODE_STATE) {
                 uint64_t J = 0;
                 for (int j = 0; j < M; ++j)
                     if (bcol[(size_t)j * K] > 0.f) J |= 1ull << j;
-                if (MODE == MODE_HIST)
-                    sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, hs);
-                else
+                if (MODE == MODE_HIST) {
+                    WindowSink ws = make_window_sink(P, S, L, smem);
+                    sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, ws);
+                } else {
+                    RefineSink rs = make_refine_sink(P, S, L, smem);
                     sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, rs);
+                }
             }
         }
         __syncthreads();
@@ -486,7 +836,7 @@ int max_optin_smem() {
     return v;
 }
 
-constexpr int CSR_THREADS = 256;
+constexpr int CSR_THREADS = 512;
 constexpr int DENSE_THREADS = 256;
 
 int dense_tile_users(const Params &P) {
@@ -504,13 +854,17 @@ cudaError_t launch_t(const Params &P, const Scratch &S, const double *lam, uint3
     if (P.layout == KP_B_CSR) {
         SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE);
         auto kern = csr_pass_kernel<MAXM, MODE, CSR_THREADS>;
-        static bool attr_done = false;  // once per instantiation, before any stream capture
-        if (!attr_done) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin_smem());
+        static int max_dyn = -1;  // once per instantiation, before any stream capture
+        if (max_dyn < 0) {
+            cudaFuncAttributes fa;
+            cudaError_t e = cudaFuncGetAttributes(&fa, kern);
             if (e != cudaSuccess) return e;
-            attr_done = true;
+            const int md = max_optin_smem() - (int)fa.sharedSizeBytes;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, md);
+            if (e != cudaSuccess) return e;
+            max_dyn = md;
         }
-        if (L.total > (size_t)max_optin_smem()) return cudaErrorInvalidConfiguration;
+        if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
         if (occupancy_out) {
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, CSR_THREADS, L.total);
         }
@@ -520,13 +874,17 @@ cudaError_t launch_t(const Params &P, const Scratch &S, const double *lam, uint3
         int T = dense_tile_users(P);
         SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, DENSE_THREADS, T, MODE);
         auto kern = dense_pass_kernel<MAXM, MODE, DENSE_THREADS>;
-        static bool attr_done = false;  // once per instantiation, before any stream capture
-        if (!attr_done) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin_smem());
+        static int max_dyn = -1;  // once per instantiation, before any stream capture
+        if (max_dyn < 0) {
+            cudaFuncAttributes fa;
+            cudaError_t e = cudaFuncGetAttributes(&fa, kern);
             if (e != cudaSuccess) return e;
-            attr_done = true;
+            const int md = max_optin_smem() - (int)fa.sharedSizeBytes;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, md);
+            if (e != cudaSuccess) return e;
+            max_dyn = md;
         }
-        if (L.total > (size_t)max_optin_smem()) return cudaErrorInvalidConfiguration;
+        if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
         if (occupancy_out) {
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, DENSE_THREADS, L.total);
         }
@@ -547,6 +905,8 @@ cudaError_t launch_m(const Params &P, const Scratch &S, const double *lam, int m
 
 cudaError_t dispatch(const Params &P, const Scratch &S, const double *lam, int mode, int round,
                      uint32_t *x_bits, cudaStream_t st, int *occ) {
+    if (P.M <= 8) return launch_m<8>(P, S, lam, mode, round, x_bits, st, occ);
+    if (P.M <= 10) return launch_m<10>(P, S, lam, mode, round, x_bits, st, occ);
     if (P.M <= 16) return launch_m<16>(P, S, lam, mode, round, x_bits, st, occ);
     return launch_m<64>(P, S, lam, mode, round, x_bits, st, occ);
 }
@@ -570,12 +930,17 @@ int pass_grid_size(const Params &P) {
     if (dispatch(P, dummy, nullptr, MODE_REFINE, 0, nullptr, 0, &occ2) == cudaSuccess && occ2 >= 1 &&
         occ2 < occ)
         occ = occ2;
+    int occ3 = 0;
+    if (dispatch(P, dummy, nullptr, MODE_STATE, 0, nullptr, 0, &occ3) == cudaSuccess && occ3 >= 1 &&
+        occ3 < occ)
+        occ = occ3;
+    (void)cudaGetLastError();  // the queries above report failures through their return values
     if (occ > 4) occ = 4;
     return sms * occ;
 }
 
 size_t pass_smem_bytes(const Params &P, int mode) {
-    int maxm = P.M <= 16 ? 16 : 64;
+    int maxm = P.M <= 8 ? 8 : (P.M <= 10 ? 10 : (P.M <= 16 ? 16 : 64));
     if (P.layout == KP_B_CSR) return smem_layout(KP_B_CSR, P.K, P.M, maxm, CSR_THREADS, 0, mode).total;
     return smem_layout(KP_B_DENSE, P.K, P.M, maxm, DENSE_THREADS, dense_tile_users(P), mode).total;
 }

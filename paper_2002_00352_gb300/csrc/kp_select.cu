@@ -4,9 +4,11 @@
 //                    (Eq. (5)) and the dual-descent update (Eq. (14)).
 //   select_kernel    the Reduce of Algorithm 4 for every knapsack: find the
 //                    breakpoint at which the mass accumulated from the top
-//                    first exceeds B_k, from the bucket histogram and then
-//                    exactly among the buffered breakpoints (radix selection
-//                    on the FP32 bit patterns, 8 bits per round).
+//                    first exceeds B_k, from the exact masses above / inside /
+//                    below the window and then exactly among the buffered
+//                    breakpoints (radix selection on the FP32 bit patterns,
+//                    8 bits per round), or by re-run passes with 256-way
+//                    sub-histograms when the crossing is outside the window.
 //   backward_kernel  Danskin gradient of the dual function.
 //   validate_kernel  checks of Sec. 2's data assumptions at creation.
 #include <cfloat>
@@ -33,11 +35,10 @@ __global__ void finalize_kernel(Params P, Scratch S, const double *lam, double *
                                 int do_dd) {
     const int K = P.K;
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int q = 0; q < S.G; ++q) {
-            a += S.dual_part[q];
-            b += S.primal_part[q];
-        }
+        const double io = ldexp(1.0, -P.fixo);
+        const double a = (double)S.objfix[0] * io, b = (double)S.objfix[1] * io;
+        S.objfix[0] = 0ull;
+        S.objfix[1] = 0ull;
         if (dual) *dual = a;
         if (primal) *primal = b;
         if (g) {
@@ -68,7 +69,6 @@ __device__ uint32_t exact_select(const Scratch &S, const Params &P, int k, uint3
     __shared__ uint32_t s_lo, s_w;
     __shared__ unsigned long long s_need;
     __shared__ int s_ok;
-    const float scale = __uint_as_float((uint32_t)(127 + P.fixs) << 23);
     if (threadIdx.x == 0) {
         s_lo = lo;
         s_w = hi - lo;
@@ -90,7 +90,7 @@ __device__ uint32_t exact_select(const Scratch &S, const Params &P, int k, uint3
             for (uint32_t s = threadIdx.x; s < cnt; s += blockDim.x) {
                 const uint2 e = base[s];
                 const uint32_t off = e.x - clo;
-                if (e.x >= clo && off < width) atomicAdd(&h[off >> sh], fixmass(__uint_as_float(e.y), scale));
+                if (e.x >= clo && off < width) atomicAdd(&h[off >> sh], fixmass(__uint_as_float(e.y), P.fixs));
             }
         }
         __syncthreads();
@@ -123,17 +123,38 @@ __device__ uint32_t exact_select(const Scratch &S, const Params &P, int k, uint3
     return s_lo;
 }
 
-__device__ __forceinline__ void resolved(Scratch &S, SelK &sk, int k, uint32_t key,
+// Record lambda_k^{t+1} and choose the centre and window of the next pass.
+// In the damped two-cycles that synchronous coordinate descent shows, the
+// next value is closer to the value two steps back than to the last one, so
+// when the last two moves alternate in sign the centre is lambda_k^t.  The
+// half-width is twice the error of this pass's centre.
+__device__ __forceinline__ void resolved(SelK &sk, int k, uint32_t key, float lam_t,
                                          double *lam_next) {
     lam_next[k] = key ? (double)__uint_as_float(key) : 0.0;
+    const uint32_t cur = lam_t > 0.f ? __float_as_uint(lam_t) : 0u;
+    const uint32_t prev = sk.prev_key;
+    const bool osc = (key > cur && cur < prev) || (key < cur && cur > prev);
+    uint32_t pred = osc ? cur : key;
+    if (pred == 0u) pred = key ? key : (cur ? cur : sk.last_nz_key);
     if (key) {
-        int off = bucket_of(key, sk.ckey) - NB_CENTRE;
-        if (off < 0) off = -off;
-        int w = off + 1;
-        sk.w = w < WMIN ? WMIN : (w > 31 ? 31 : w);
+        const uint32_t err = key > sk.ckey ? key - sk.ckey : sk.ckey - key;
+        const int w = bitlen32(err) + 1;
+        sk.w = w < WMIN_BITS ? WMIN_BITS : (w > 30 ? 30 : w);
         sk.last_nz_key = key;
     }
+    sk.prev_key = cur;
+    sk.for_key = key;
+    sk.pred_key = pred;
     sk.state = 0;
+}
+
+__device__ __forceinline__ void unresolved(Scratch &S, SelK &sk, uint32_t lo, uint32_t hi,
+                                           unsigned long long above, int round) {
+    sk.state = 1;
+    sk.lo = lo;
+    sk.hi = hi;
+    sk.above = above;
+    atomicAdd(&S.ctr->n_unres[round + 1], 1);
 }
 
 __global__ void select_kernel(Params P, Scratch S, const double *lam, double *lam_next, int round) {
@@ -146,25 +167,72 @@ __global__ void select_kernel(Params P, Scratch S, const double *lam, double *la
     __syncthreads();
     if (round > 0 && sk.state != 1) return;
     const unsigned long long Bfix = budget_fixed(P.B[k], P.fixs);
-    const int nrow = round == 0 ? NB : NSUB;
-    unsigned long long *grow = round == 0 ? S.hist + (size_t)k * NB : S.subhist + (size_t)k * NSUB;
-    for (int q = threadIdx.x; q < nrow; q += blockDim.x) {
-        row[q] = grow[q];
-        grow[q] = 0ull;
-    }
-    __syncthreads();
+    const float lam_t = (float)lam[k];
     const uint32_t ovf = S.ovf[k];
     __syncthreads();
     if (threadIdx.x == 0) {
         S.ovf[k] = 0u;
         if (ovf) atomicAdd(&S.ctr->stats[2], 1ull);
-        // scan from the top for the bucket where the accumulated mass first exceeds B_k
-        unsigned long long above = round == 0 ? 0ull : sk.above;
-        const unsigned long long need_total = Bfix;
+    }
+    if (round == 0) {
+        // masses at/above, inside and below the window [wlo, whi)
+        const unsigned long long A = S.reg3[3 * k], W = S.reg3[3 * k + 1], Bl = S.reg3[3 * k + 2];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            S.reg3[3 * k] = 0ull;
+            S.reg3[3 * k + 1] = 0ull;
+            S.reg3[3 * k + 2] = 0ull;
+        }
+        const unsigned long long total = A + W + Bl;
+        if (total <= Bfix) {  // the whole mass fits: lambda_k = 0
+            if (threadIdx.x == 0) {
+                resolved(sk, k, 0u, lam_t, lam_next);
+                atomicAdd(&S.ctr->stats[1], 1ull);
+                S.sel[k] = sk;
+            }
+            return;
+        }
+        if (A > Bfix) {  // crossing at or above the window
+            if (threadIdx.x == 0) {
+                unresolved(S, sk, sk.whi, KEY_INF, 0ull, round);
+                S.sel[k] = sk;
+            }
+            return;
+        }
+        if (A + W > Bfix) {  // crossing inside the window
+            if (!ovf) {
+                bool ok = true;
+                const uint32_t key = exact_select(S, P, k, sk.wlo, sk.whi, Bfix - A, &ok);
+                if (threadIdx.x == 0) {
+                    if (!ok) atomicOr(&S.ctr->status, 1 << KP_ESTATE);
+                    resolved(sk, k, key, lam_t, lam_next);
+                    S.sel[k] = sk;
+                }
+            } else if (threadIdx.x == 0) {
+                unresolved(S, sk, sk.wlo, sk.whi, A, round);
+                S.sel[k] = sk;
+            }
+            return;
+        }
+        if (threadIdx.x == 0) {  // crossing below the window
+            unresolved(S, sk, 1u, sk.wlo > 1u ? sk.wlo : 2u, A + W, round);
+            S.sel[k] = sk;
+        }
+        return;
+    }
+
+    // refine round: sub-histogram of [sk.lo, sk.hi)
+    unsigned long long *grow = S.subhist + (size_t)k * NSUB;
+    for (int q = threadIdx.x; q < NSUB; q += blockDim.x) {
+        row[q] = grow[q];
+        grow[q] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         int pick = -1;
-        unsigned long long acc = above;
-        for (int b = nrow - 1; b >= 0; --b) {
-            if (acc + row[b] > need_total || (acc + row[b] < acc)) {
+        unsigned long long acc = sk.above;
+        for (int b = NSUB - 1; b >= 0; --b) {
+            if (acc + row[b] > Bfix) {
                 pick = b;
                 break;
             }
@@ -175,76 +243,36 @@ __global__ void select_kernel(Params P, Scratch S, const double *lam, double *la
     }
     __syncthreads();
     const int pick = s_pick;
-    if (pick < 0) {
-        // the whole mass fits: lambda_k = 0 (round 0), or an inconsistent refine
+    if (pick < 0) {  // inconsistent: the range does not hold the crossing
         if (threadIdx.x == 0) {
-            if (round == 0) {
-                lam_next[k] = 0.0;
-                sk.state = 0;
-                atomicAdd(&S.ctr->stats[1], 1ull);
-            } else {
-                atomicOr(&S.ctr->status, 1 << KP_ESTATE);
-                lam_next[k] = sk.lo ? (double)__uint_as_float(sk.lo) : 0.0;
-                sk.state = 0;
-            }
+            atomicOr(&S.ctr->status, 1 << KP_ESTATE);
+            resolved(sk, k, sk.lo, lam_t, lam_next);
             S.sel[k] = sk;
         }
         return;
     }
-    // key range of the picked bucket
-    uint32_t lo, hi;
-    if (round == 0) {
-        const long long c = (long long)sk.ckey;
-        long long l, h;
-        if (pick == NB_CENTRE) {
-            l = c;
-            h = c + 1;
-        } else if (pick > NB_CENTRE) {
-            const int e = pick - NB_CENTRE - 1;
-            l = c + (1ll << e);
-            h = c + (2ll << e);
-        } else {
-            const int e = NB_CENTRE - 1 - pick;
-            l = c - (2ll << e) + 1;
-            h = c - (1ll << e) + 1;
-        }
-        if (l < 0) l = 0;
-        if (h > 0x7F800000ll) h = 0x7F800000ll;
-        if (h <= l) h = l + 1;
-        lo = (uint32_t)l;
-        hi = (uint32_t)h;
-    } else {
-        const uint32_t width = sk.hi - sk.lo;
-        int sh = bitlen32(width - 1) - 8;
-        if (sh < 0) sh = 0;
-        lo = sk.lo + ((uint32_t)pick << sh);
-        const uint32_t span = sh == 0 ? 1u : (1u << sh);
-        hi = (sk.hi - lo) < span ? sk.hi : lo + span;
-    }
-    const unsigned long long above = s_above;
-    int off = pick - NB_CENTRE;
-    if (off < 0) off = -off;
-    const bool in_window = round == 0 ? (off <= sk.w) : true;
-    if (in_window && !ovf) {
+    if (!ovf) {
         bool ok = true;
-        const uint32_t key = exact_select(S, P, k, lo, hi, Bfix - above, &ok);
+        const uint32_t key = exact_select(S, P, k, sk.lo, sk.hi, Bfix - sk.above, &ok);
         if (threadIdx.x == 0) {
             if (!ok) atomicOr(&S.ctr->status, 1 << KP_ESTATE);
-            resolved(S, sk, k, key, lam_next);
+            resolved(sk, k, key, lam_t, lam_next);
             S.sel[k] = sk;
         }
         return;
     }
+    const uint32_t width = sk.hi - sk.lo;
+    int sh = bitlen32(width - 1) - 8;
+    if (sh < 0) sh = 0;
+    const uint32_t lo = sk.lo + ((uint32_t)pick << sh);
+    const uint32_t span = sh == 0 ? 1u : (1u << sh);
+    const uint32_t hi = (sk.hi - lo) < span ? sk.hi : lo + span;
     if (threadIdx.x == 0) {
         if (round >= MAX_REFINE) {
             atomicOr(&S.ctr->status, 1 << KP_ESTATE);
-            resolved(S, sk, k, lo, lam_next);
+            resolved(sk, k, lo, lam_t, lam_next);
         } else {
-            sk.state = 1;
-            sk.lo = lo;
-            sk.hi = hi;
-            sk.above = above;
-            atomicAdd(&S.ctr->n_unres[round + 1], 1);
+            unresolved(S, sk, lo, hi, s_above, round);
         }
         S.sel[k] = sk;
     }
@@ -280,8 +308,12 @@ __global__ void validate_kernel(Params P, uint32_t *flags) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t bad = 0, maxb = 0;
     const int M = P.M, K = P.K;
-    for (int64_t q = tid; q < P.N * M; q += stride)
-        if (!finite_nonneg(P.p[q])) bad |= 1u;
+    uint32_t maxp = 0;
+    for (int64_t q = tid; q < P.N * M; q += stride) {
+        const float v = P.p[q];
+        if (!finite_nonneg(v)) bad |= 1u;
+        else maxp = max(maxp, __float_as_uint(v));
+    }
     if (P.layout == KP_B_DENSE) {
         const int64_t tot = P.N * (int64_t)M * K;
         for (int64_t q = tid; q < tot; q += stride) {
@@ -315,6 +347,7 @@ __global__ void validate_kernel(Params P, uint32_t *flags) {
     }
     if (bad) atomicOr(&flags[0], bad);
     if (maxb) atomicMax(&flags[1], maxb);
+    if (maxp) atomicMax(&flags[2], maxp);
 }
 
 int sm_count() {
@@ -328,7 +361,40 @@ int sm_count() {
     return sms;
 }
 
+// For every user with at most 32 entries: bit e set iff entry e has b > 0 and
+// another item of the same user has an entry with the same knapsack and b > 0.
+__global__ void shmask_kernel(Params P, uint32_t *shmask) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
+        const int64_t e0 = P.uoff[i];
+        const int64_t nnz = P.uoff[i + 1] - e0;
+        if (nnz > 32) {
+            shmask[i] = 0u;
+            continue;
+        }
+        int owner[32];
+        int e = 0;
+        for (int j = 0; j < P.M; ++j) {
+            const int c = P.innz[i * P.M + j];
+            for (int q = 0; q < c && e < 32; ++q) owner[e++] = j;
+        }
+        uint32_t m = 0;
+        for (int a = 0; a < (int)nnz; ++a) {
+            if (!(P.val[e0 + a] > 0.f)) continue;
+            const int ka = P.kidx[e0 + a];
+            for (int b = 0; b < (int)nnz; ++b)
+                if (owner[b] != owner[a] && P.kidx[e0 + b] == ka && P.val[e0 + b] > 0.f) m |= 1u << a;
+        }
+        shmask[i] = m;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_shmask(const Params &P, uint32_t *shmask, cudaStream_t st) {
+    shmask_kernel<<<sm_count() * 8, 256, 0, st>>>(P, shmask);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_finalize(const Params &P, const Scratch &S, const double *lambda, double *R,
                             double *dual, double *primal, double *g, double alpha,
