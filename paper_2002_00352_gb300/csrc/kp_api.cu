@@ -153,7 +153,15 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
     kp_status st = KP_OK;
     // device scan of the instance (Sec. 2 data assumptions)
     uint32_t *flags = nullptr;
-    if ((st = alloc(h, &flags, 3, "validation flags")) != KP_OK) goto fail_out;
+    if ((st = alloc(h, &flags, 5, "validation flags")) != KP_OK) goto fail_out;
+    {
+        const uint32_t init[5] = {0u, 0u, 0u, 0xffffffffu, 0u};
+        cudaError_t e0 = cudaMemcpy(flags, init, sizeof(init), cudaMemcpyHostToDevice);
+        if (e0 != cudaSuccess) {
+            st = cuda_fail(e0, "validation flags");
+            goto fail_out;
+        }
+    }
     {
         cudaError_t e = kp::launch_validate(P, flags, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -161,7 +169,7 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
             st = cuda_fail(e, "validate");
             goto fail_out;
         }
-        uint32_t hf[3] = {0, 0, 0};
+        uint32_t hf[5] = {0, 0, 0, 0, 0};
         e = cudaMemcpy(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
             st = cuda_fail(e, "validate copy");
@@ -190,6 +198,15 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
                 goto fail_out;
             }
             count = (double)(ends[1] - ends[0]);
+            P.uoff0 = ends[0];
+            if (hf[3] == hf[4] && (hf[3] == 1 || hf[3] == 2)) {
+                P.creg = (int)hf[3];
+                const bool mexact = P.M == 8 || P.M == 10 || P.M == 16;
+                const uintptr_t pp = (uintptr_t)P.p, vp = (uintptr_t)(P.val + P.uoff0),
+                                kp2 = (uintptr_t)(P.kidx + P.uoff0);
+                P.vec = mexact && (pp % 8 == 0) && (vp % 16 == 0) && (kp2 % 8 == 0) &&
+                        ((P.M * P.creg) % 4 == 0);
+            }
         }
         // fixed-point mass: every per-knapsack sum is below count * max b
         double bound = count * (double)maxb + 1.0;

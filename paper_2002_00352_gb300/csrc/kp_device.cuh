@@ -190,20 +190,18 @@ __device__ __forceinline__ unsigned long long fixmass(float v, int s) {
 //   pt[j*ps]   p~_j at lambda^t;  s[j*ss]  b_jk (0 for items not in J)
 //   J          items with b_jk > 0 (the lines that move with lambda_k)
 //   lamk       lambda_k^t in FP32
+//   w          the greedy selection among the items not in J (the fixed
+//              lines): it is the selection at lambda_k = +inf, and no other
+//              fixed item can ever enter
+// The sorted order of the positive lines is maintained as lambda_k falls;
+// only zero crossings and adjacent swaps can change the selection.
 // ---------------------------------------------------------------------------
 template <int MAXM, class Sink>
-__device__ void sweep_k(const float *pt, int ps, const float *s, int ss, int M, uint64_t J,
-                        float lamk, const Tree &t, int k, Sink &sink) {
+__device__ __forceinline__ void sweep_from(const float *pt, int ps, const float *s, int ss, int M,
+                                           uint64_t J, float lamk, const Tree &t, int k, Walk w,
+                                           Sink &sink) {
     float la[MAXM], ls[MAXM], zc[MAXM], pe[MAXM];
     int ord[MAXM], zl[MAXM];
-
-    // items whose line does not move: only the greedy selection among them at
-    // lambda_k = +inf can ever be selected (no fixed item can enter later)
-    uint64_t fcand = 0;
-    for (int j = 0; j < M; ++j)
-        if (!((J >> j) & 1ull) && pt[j * ps] > 0.f) fcand |= 1ull << j;
-    Walk w;
-    greedy_walk(pt, ps, fcand, t, w);
 
     int np = 0;
     uint64_t r = w.sel;
@@ -300,6 +298,34 @@ __device__ void sweep_k(const float *pt, int ps, const float *s, int ss, int M, 
             }
         }
     }
+}
+
+// The walk state (counters, full sets) of a given selection.
+__device__ __forceinline__ Walk walk_of(uint64_t sel, const Tree &t) {
+    Walk w;
+    w.sel = 0;
+    w.rej = 0;
+    w.full = 0;
+    w.clo = 0;
+    w.chi = 0;
+    uint64_t r = sel;
+    while (r) {
+        const int j = __ffsll((long long)r) - 1;
+        r &= r - 1;
+        walk_add(w, t, j);
+    }
+    return w;
+}
+
+template <int MAXM, class Sink>
+__device__ void sweep_k(const float *pt, int ps, const float *s, int ss, int M, uint64_t J,
+                        float lamk, const Tree &t, int k, Sink &sink) {
+    uint64_t fcand = 0;
+    for (int j = 0; j < M; ++j)
+        if (!((J >> j) & 1ull) && pt[j * ps] > 0.f) fcand |= 1ull << j;
+    Walk w;
+    greedy_walk(pt, ps, fcand, t, w);
+    sweep_from<MAXM>(pt, ps, s, ss, M, J, lamk, t, k, w, sink);
 }
 
 // ---------------------------------------------------------------------------

@@ -67,6 +67,9 @@ struct Params {
     const double *B;
     int32_t fixs;              // fixed-point shift of b sums: units of 2^-fixs
     int32_t fixo;              // fixed-point shift of the objective sums
+    int32_t creg;              // CSR: every item has exactly creg entries (0: not regular)
+    int32_t vec;               // CSR regular rows aligned for vector loads (M in {8, 10, 16})
+    int64_t uoff0;             // csr_user_off[0]
     Tree tree;
 };
 

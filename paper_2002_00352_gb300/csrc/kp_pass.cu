@@ -63,8 +63,8 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     s.red = o;
     o = align16(o + 2 * 8 * 32);
     if (layout == KP_B_CSR) {
-        s.rows = o;  // p~ rows of users with shared-knapsack sweeps
-        if (mode != MODE_STATE) o = align16(o + 4 * (size_t)threads * maxm);
+        s.rows = o;  // per thread: p~ row and rank masks (for shared-knapsack sweeps), margin row
+        if (mode != MODE_STATE) o = align16(o + 3 * 4 * (size_t)threads * maxm);
         s.tile_p = s.tile_b = s.selm = o;
     } else {
         s.tile_p = o;
@@ -242,7 +242,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *s_scan) {
 }
 
 template <int MAXM, int MODE, class Sink>
-__device__ __forceinline__ void csr_user(const Params &P, const Scratch &S, int64_t i, int64_t e0,
+__device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t i, int64_t e0,
                                          int nnz, const float *lamf, float *pt, float *mg,
                                          unsigned long long *rfix, unsigned long long &dsum, unsigned long long &psum,
                                          uint32_t *x_bits, Sink &sink) {
@@ -390,15 +390,23 @@ __device__ __forceinline__ void csr_user(const Params &P, const Scratch &S, int6
 // Lean per-user routine for M <= MAXM <= 16 and at most 32 entries: reduced
 // costs, decisions and margins live in registers, loops run over the items in
 // compile-time order with predication, so the lanes of a warp stay together.
+// C > 0: every item has exactly C entries (checked at creation), so entry e
+// of the user belongs to item e / C and all entry loops unroll; with
+// P.vec the user's rows are read with vector loads.  C = 0: counts are read
+// from csr_item_nnz.
 //   Algorithm 1 is evaluated in its literal bottom-up form: beats[j] is the set
 //   of items ranked before j (larger p~, ties to the lower index); at set S_l
 //   an item survives if fewer than C_l survivors of S_l rank before it.
-template <int MAXM, int MODE, class Sink>
+// Returns the entries whose knapsack another item of the user also uses and
+// that are the first of their knapsack (they need the kinetic sweep); the
+// user's p~ row is then left in prow.
+template <int MAXM, int C, int MODE, class Sink>
 __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch &S, int64_t i,
                                                   int64_t e0, const float4 *kinfo,
                                                   unsigned long long *rfix, unsigned long long &dsum,
                                                   unsigned long long &psum, uint32_t *x_bits,
                                                   Sink &sink, float *prow) {
+    constexpr int EC = C > 0 ? MAXM * C : 1;
     const int M = P.M;
     const Tree &T = P.tree;
     const float *pr = P.p + (size_t)i * M;
@@ -408,13 +416,71 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
 
     float pt[MAXM];
     int cnt[MAXM];
+    float vv[EC];
+    int kk[EC];
+    if constexpr (C > 0) {
+        if (P.vec) {  // M == MAXM and the rows are aligned for vector loads
+            if constexpr (MAXM % 2 == 0) {
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-        pt[j] = j < M ? __ldg(pr + j) : 0.f;
-        cnt[j] = j < M ? (int)nzr[j] : 0;
+                for (int q = 0; q < MAXM / 2; ++q) {
+                    const float2 t = __ldg(reinterpret_cast<const float2 *>(pr) + q);
+                    pt[2 * q] = t.x;
+                    pt[2 * q + 1] = t.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < MAXM; ++j) pt[j] = __ldg(pr + j);
+            }
+            if constexpr (EC % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < EC / 4; ++q) {
+                    const float4 t = __ldg(reinterpret_cast<const float4 *>(val) + q);
+                    vv[4 * q] = t.x;
+                    vv[4 * q + 1] = t.y;
+                    vv[4 * q + 2] = t.z;
+                    vv[4 * q + 3] = t.w;
+                    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(kid) + q);
+                    kk[4 * q] = (int)(int16_t)(u.x & 0xffffu);
+                    kk[4 * q + 1] = (int)(int16_t)(u.x >> 16);
+                    kk[4 * q + 2] = (int)(int16_t)(u.y & 0xffffu);
+                    kk[4 * q + 3] = (int)(int16_t)(u.y >> 16);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < EC; ++e) {
+                    vv[e] = __ldg(val + e);
+                    kk[e] = kid[e];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < MAXM; ++j) pt[j] = j < M ? __ldg(pr + j) : 0.f;
+#pragma unroll
+            for (int e = 0; e < EC; ++e) {
+                const bool in = e < M * C;
+                vv[e] = in ? __ldg(val + e) : 0.f;
+                kk[e] = in ? (int)kid[e] : 0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) cnt[j] = j < M ? C : 0;
+    } else {
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+            pt[j] = j < M ? __ldg(pr + j) : 0.f;
+            cnt[j] = j < M ? (int)nzr[j] : 0;
+        }
     }
     // Sec. 4.2 reduced costs
-    {
+    if constexpr (C > 0) {
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+            float acc = pt[j];
+#pragma unroll
+            for (int q = 0; q < C; ++q) acc = fmaf(-kinfo[kk[j * C + q]].x, vv[j * C + q], acc);
+            pt[j] = acc;
+        }
+    } else {
         int e = 0;
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
@@ -455,76 +521,80 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
 
     if (MODE != MODE_REFINE) {
         if (x_bits) x_bits[(size_t)i * P.W] = G;
-        int e = 0;
         float du = 0.f, pu = 0.f;
+        if constexpr (C > 0) {
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-            if ((G >> j) & 1u) {
-                du += pt[j];
-                pu += __ldg(pr + j);
-                for (int q = 0; q < cnt[j]; ++q)
-                    shared_add_u64(&rfix[kid[e + q]], fixmass(__ldg(val + e + q), P.fixs));
+            for (int j = 0; j < MAXM; ++j)
+                if ((G >> j) & 1u) {
+                    du += pt[j];
+                    pu += __ldg(pr + j);
+#pragma unroll
+                    for (int q = 0; q < C; ++q) shared_add_u64(&rfix[kk[j * C + q]], fixmass(vv[j * C + q], P.fixs));
+                }
+        } else {
+            int e = 0;
+#pragma unroll
+            for (int j = 0; j < MAXM; ++j) {
+                if ((G >> j) & 1u) {
+                    du += pt[j];
+                    pu += __ldg(pr + j);
+                    for (int q = 0; q < cnt[j]; ++q)
+                        shared_add_u64(&rfix[kid[e + q]], fixmass(__ldg(val + e + q), P.fixs));
+                }
+                e += cnt[j];
             }
-            e += cnt[j];
         }
         dsum += fixmass(du, P.fixo);
         psum += fixmass(pu, P.fixo);
     }
-    if (MODE == MODE_STATE) return 0u;
-
-    // exchange thresholds theta_j and margins p~_j - theta_j
-    float minSel[KP_MAX_L], maxCut[KP_MAX_L];
-    for (int l = 0; l < T.L; ++l) {
-        minSel[l] = FLT_MAX;
-        maxCut[l] = 0.f;
-    }
-    const uint32_t rej = pos & ~G;
+    if constexpr (MODE == MODE_STATE) {
+        return 0u;
+    } else {
+        // exchange thresholds theta_j and margins p~_j - theta_j, without
+        // data-dependent branches: for every full set l, minSel[l] is the
+        // weakest selected item of l and maxCut[l] the best rejected item whose
+        // deepest full set is l
+        float minSel[KP_MAX_L], maxCut[KP_MAX_L];
+        const uint32_t rej = pos & ~G;
+        int dy[MAXM];
 #pragma unroll
-    for (int y = 0; y < MAXM; ++y) {
-        if (y < M) {
-            uint32_t path = T.ipath[y];
-            if ((G >> y) & 1u) {
-                while (path) {
-                    const int l = __ffs(path) - 1;
-                    path &= path - 1;
-                    minSel[l] = fminf(minSel[l], pt[y]);
-                }
-            } else if ((rej >> y) & 1u) {
-                const uint32_t f = path & full;
-                if (f) {
-                    const int l = __ffs(f) - 1;
-                    maxCut[l] = fmaxf(maxCut[l], pt[y]);
-                }
-            }
-        }
-    }
-    float mg[MAXM];
+        for (int y = 0; y < MAXM; ++y) dy[y] = __ffs(T.ipath[y] & full) - 1;
+        for (int l = 0; l < T.L; ++l) {
+            const uint32_t selL = G & (uint32_t)T.items[l];
+            float mn = FLT_MAX, mx = 0.f;
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-        float th = 0.f;
-        if (j < M) {
-            uint32_t path = T.ipath[j];
-            if ((G >> j) & 1u) {
-                while (path) {
-                    const int l = __ffs(path) - 1;
-                    path &= path - 1;
-                    th = fmaxf(th, maxCut[l]);
-                }
-            } else {
-                const uint32_t f = path & full;
-                if (f) th = minSel[__ffs(f) - 1];
+            for (int j = 0; j < MAXM; ++j) {
+                mn = ((selL >> j) & 1u) ? fminf(mn, pt[j]) : mn;
+                mx = (((rej >> j) & 1u) && dy[j] == l) ? fmaxf(mx, pt[j]) : mx;
             }
+            minSel[l] = mn;
+            maxCut[l] = mx;
         }
-        mg[j] = pt[j] - th;
-    }
-    // Algorithm 4 Map: closed form for knapsacks only one item touches
-    const uint32_t shm = S.shmask[i];
-    uint32_t pending = 0u;
-    {
-        int e = 0;
+        float *mrow = prow + (size_t)blockDim.x * MAXM;  // this thread's margin row
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
-            for (int q = 0; q < cnt[j]; ++q, ++e) {
+            float ts = 0.f;
+            uint32_t path = T.ipath[j];
+            while (path) {  // the same path in every lane
+                const int l = __ffs(path) - 1;
+                path &= path - 1;
+                ts = fmaxf(ts, maxCut[l]);
+            }
+            const float tn = dy[j] >= 0 ? minSel[dy[j] < 0 ? 0 : dy[j]] : 0.f;
+            mrow[j] = pt[j] - (((G >> j) & 1u) ? ts : tn);
+        }
+        // Algorithm 4 Map: closed form for knapsacks only one item touches.  One
+        // rolled copy of the emission body keeps the code in the instruction
+        // cache; entries are re-read from L1.
+        const uint32_t shm = S.shmask[i];
+        uint32_t pending = 0u;
+        int e = 0;
+#pragma unroll 1
+        for (int j = 0; j < M; ++j) {
+            const float m = mrow[j];
+            const int c = C > 0 ? C : (int)nzr[j];
+#pragma unroll 1
+            for (int q = 0; q < c; ++q, ++e) {
                 const int k = kid[e];
                 if ((shm >> e) & 1u) {
                     uint32_t earlier = shm & ((1u << e) - 1u);
@@ -532,7 +602,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                     while (earlier) {
                         const int f = __ffs(earlier) - 1;
                         earlier &= earlier - 1;
-                        if (kid[f] == k) firstk = false;
+                        if ((int)kid[f] == k) firstk = false;
                     }
                     if (firstk) pending |= 1u << e;
                     continue;
@@ -540,56 +610,75 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 const float v = __ldg(val + e);
                 if (v > 0.f) {
                     const float4 ki = kinfo[k];
-                    sink.emit_ki(k, ki, ki.x + __fdividef(mg[j], v), v);
+                    sink.emit_ki(k, ki, ki.x + __fdividef(m, v), v);
                 }
             }
         }
-    }
-    if (pending) {
+        if (pending) {
+            uint32_t *brow = reinterpret_cast<uint32_t *>(prow + 2 * (size_t)blockDim.x * MAXM);
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j) prow[j] = pt[j];
+            for (int j = 0; j < MAXM; ++j) {
+                prow[j] = pt[j];
+                brow[j] = beats[j];
+            }
+        }
+        return pending;
     }
-    return pending;
 }
 
 // One shared-knapsack sweep: the owner's p~ row is in shared memory, its
 // entries are read again to collect the slopes b_jk of knapsack k.
-template <int MAXM, class Sink>
-__device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo, const float *prow,
-                                           int64_t i, int64_t e0, int e, Sink &sink) {
+template <int MAXM, int C, class Sink>
+__device__ __noinline__ void sweep_task(const Params &P, const float4 *kinfo, const float *prow,
+                                        const uint32_t *brow, int64_t i, int64_t e0, int e, Sink &sink) {
     const int M = P.M;
+    const Tree &T = P.tree;
     const uint8_t *nzr = P.innz + (size_t)i * M;
     const float *val = P.val + e0;
     const int16_t *kid = P.kidx + e0;
     const int k = kid[e];
     float sv[MAXM];
-    uint64_t J = 0;
+    uint32_t J = 0, pos = 0;
     int f = 0;
     for (int j2 = 0; j2 < M; ++j2) {
-        const int c2 = nzr[j2];
+        const int c2 = C > 0 ? C : (int)nzr[j2];
         sv[j2] = 0.f;
+        if (prow[j2] > 0.f) pos |= 1u << j2;
         for (int q2 = 0; q2 < c2; ++q2, ++f)
             if (kid[f] == k) {
                 const float vv = __ldg(val + f);
                 if (vv > 0.f) {
                     sv[j2] = vv;
-                    J |= 1ull << j2;
+                    J |= 1u << j2;
                 }
             }
     }
-    sweep_k<MAXM>(prow, 1, sv, 1, M, J, kinfo[k].x, P.tree, k, sink);
+    // selection among the fixed lines: Algorithm 1 over pos \ J with the
+    // owner's rank masks
+    uint32_t SF = pos & ~J;
+    for (int l = 0; l < T.L; ++l) {
+        const uint32_t inl = SF & (uint32_t)T.items[l];
+        const int cap = T.cap[l];
+        uint32_t drop = 0u;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+            if (((inl >> j) & 1u) && __popc(brow[j] & inl) >= cap) drop |= 1u << j;
+        SF &= ~drop;
+    }
+    sweep_from<MAXM>(prow, 1, sv, 1, M, J, kinfo[k].x, T, k, walk_of(SF, T), sink);
 }
 
 // The sweeps of a warp's users are pooled and dealt round-robin to its lanes,
 // so that a user with several shared knapsacks does not keep 31 lanes idle.
 // Called by every lane of the warp.
-template <int MAXM, int THREADS, class Sink>
+template <int MAXM, int C, int THREADS, class Sink>
 __device__ __forceinline__ void warp_sweeps(const Params &P, const float4 *kinfo, float *rows,
                                             int64_t i, int64_t e0, uint32_t pending, Sink &sink) {
     constexpr int QCAP = 64;
     __shared__ uint32_t q[THREADS / 32][QCAP];
     __shared__ long long wi[THREADS], we0[THREADS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wbase = threadIdx.x & ~31;
+    const uint32_t *brows = reinterpret_cast<const uint32_t *>(rows + 2 * (size_t)THREADS * MAXM);
     const int n = __popc(pending);
     int x = n;
 #pragma unroll
@@ -616,7 +705,7 @@ __device__ __forceinline__ void warp_sweeps(const Params &P, const float4 *kinfo
     for (int t = lane; t < nq; t += 32) {
         const uint32_t d = q[warp][t];
         const int owner = wbase + (int)(d >> 5);
-        sweep_task<MAXM>(P, kinfo, rows + (size_t)owner * MAXM, wi[owner], we0[owner], (int)(d & 31u), sink);
+        sweep_task<MAXM, C>(P, kinfo, rows + (size_t)owner * MAXM, brows + (size_t)owner * MAXM, wi[owner], we0[owner], (int)(d & 31u), sink);
     }
     // tasks beyond the queue's capacity stay with their owners
     slot = x - n;
@@ -624,13 +713,13 @@ __device__ __forceinline__ void warp_sweeps(const Params &P, const float4 *kinfo
     while (pm) {
         const int e = __ffs(pm) - 1;
         pm &= pm - 1;
-        if (slot >= QCAP) sweep_task<MAXM>(P, kinfo, rows + (size_t)threadIdx.x * MAXM, i, e0, e, sink);
+        if (slot >= QCAP) sweep_task<MAXM, C>(P, kinfo, rows + (size_t)threadIdx.x * MAXM, brows + (size_t)threadIdx.x * MAXM, i, e0, e, sink);
         ++slot;
     }
     __syncwarp();
 }
 
-template <int MAXM, int MODE, int THREADS, class Sink>
+template <int MAXM, int C, int MODE, int THREADS, class Sink>
 __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsigned char *smem,
                                          const SmemLayout &L, uint32_t *x_bits, Sink &sink,
                                          unsigned long long &dsum, unsigned long long &psum) {
@@ -640,25 +729,32 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
     const float *lamf = (const float *)(smem + L.lamf);
     const float4 *kinfo = (const float4 *)(smem + L.kinfo);
     unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
+    float *rows = (float *)(smem + L.rows);
     for (int64_t base = (int64_t)blockIdx.x * THREADS; base < P.N; base += (int64_t)gridDim.x * THREADS) {
         const int64_t i = base + threadIdx.x;
         const bool valid = i < P.N;
-        if (threadIdx.x == 0) s_base = P.uoff[base];
-        int nnz = 0;
-        if (valid) {
-            const uint8_t *nzr = P.innz + (size_t)i * M;
-            for (int j = 0; j < M; ++j) nnz += nzr[j];
+        int64_t e0;
+        int nnz;
+        if constexpr (C > 0) {
+            nnz = M * C;
+            e0 = P.uoff0 + i * (int64_t)nnz;
+        } else {
+            if (threadIdx.x == 0) s_base = P.uoff[base];
+            nnz = 0;
+            if (valid) {
+                const uint8_t *nzr = P.innz + (size_t)i * M;
+                for (int j = 0; j < M; ++j) nnz += nzr[j];
+            }
+            const int excl = block_excl_scan<THREADS>(nnz, s_scan);
+            e0 = s_base + excl;
         }
-        const int excl = block_excl_scan<THREADS>(nnz, s_scan);
-        const int64_t e0 = s_base + excl;
         uint32_t pending = 0u;
-        float *rows = (float *)(smem + L.rows);
         if (valid) {
             bool done = false;
             if constexpr (MAXM <= 16) {
                 if (nnz <= 32) {
-                    pending = csr_user_fast<MAXM, MODE>(P, S, i, e0, kinfo, rfix, dsum, psum, x_bits, sink,
-                                                        rows + (size_t)threadIdx.x * MAXM);
+                    pending = csr_user_fast<MAXM, C, MODE>(P, S, i, e0, kinfo, rfix, dsum, psum, x_bits,
+                                                           sink, rows + (size_t)threadIdx.x * MAXM);
                     done = true;
                 }
             }
@@ -668,13 +764,13 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
             }
         }
         if constexpr (MODE != MODE_STATE) {
-            if constexpr (MAXM <= 16) warp_sweeps<MAXM, THREADS>(P, kinfo, rows, i, e0, pending, sink);
+            if constexpr (MAXM <= 16) warp_sweeps<MAXM, C, THREADS>(P, kinfo, rows, i, e0, pending, sink);
         }
-        __syncthreads();
+        if constexpr (C == 0) __syncthreads();
     }
 }
 
-template <int MAXM, int MODE, int THREADS>
+template <int MAXM, int C, int MODE, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch S, const double *lam,
                                                               uint32_t *x_bits, int round) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -686,13 +782,13 @@ __global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch 
     unsigned long long dsum = 0ull, psum = 0ull;
     if (MODE == MODE_HIST) {
         WindowSink ws = make_window_sink(P, S, L, smem);
-        csr_loop<MAXM, MODE, THREADS>(P, S, smem, L, x_bits, ws, dsum, psum);
+        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, ws, dsum, psum);
     } else if (MODE == MODE_REFINE) {
         RefineSink rs = make_refine_sink(P, S, L, smem);
-        csr_loop<MAXM, MODE, THREADS>(P, S, smem, L, x_bits, rs, dsum, psum);
+        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, rs, dsum, psum);
     } else {
         NullSink ns;
-        csr_loop<MAXM, MODE, THREADS>(P, S, smem, L, x_bits, ns, dsum, psum);
+        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, ns, dsum, psum);
     }
     flush_block_state<MODE>(P, S, L, smem, dsum, psum);
 }
@@ -848,49 +944,59 @@ int dense_tile_users(const Params &P) {
     return (int)T;
 }
 
+template <class Kern>
+cudaError_t prepare_kernel(Kern kern, int *max_dyn) {
+    if (*max_dyn >= 0) return cudaSuccess;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    const int md = max_optin_smem() - (int)fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, md);
+    if (e != cudaSuccess) return e;
+    *max_dyn = md;
+    return cudaSuccess;
+}
+
+template <int MAXM, int C, int MODE>
+cudaError_t launch_csr(const Params &P, const Scratch &S, const double *lam, uint32_t *x_bits,
+                       int round, cudaStream_t st, int *occupancy_out) {
+    SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE);
+    auto kern = csr_pass_kernel<MAXM, C, MODE, CSR_THREADS>;
+    static int max_dyn = -1;  // once per instantiation, before any stream capture
+    cudaError_t e = prepare_kernel(kern, &max_dyn);
+    if (e != cudaSuccess) return e;
+    if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
+    if (occupancy_out)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, CSR_THREADS, L.total);
+    kern<<<S.G, CSR_THREADS, L.total, st>>>(P, S, lam, x_bits, round);
+    return cudaGetLastError();
+}
+
+template <int MAXM, int MODE>
+cudaError_t launch_dense(const Params &P, const Scratch &S, const double *lam, uint32_t *x_bits,
+                         int round, cudaStream_t st, int *occupancy_out) {
+    int T = dense_tile_users(P);
+    SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, DENSE_THREADS, T, MODE);
+    auto kern = dense_pass_kernel<MAXM, MODE, DENSE_THREADS>;
+    static int max_dyn = -1;
+    cudaError_t e = prepare_kernel(kern, &max_dyn);
+    if (e != cudaSuccess) return e;
+    if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
+    if (occupancy_out)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, DENSE_THREADS, L.total);
+    kern<<<S.G, DENSE_THREADS, L.total, st>>>(P, S, lam, x_bits, round, T);
+    return cudaGetLastError();
+}
+
 template <int MAXM, int MODE>
 cudaError_t launch_t(const Params &P, const Scratch &S, const double *lam, uint32_t *x_bits,
-                     int round, cudaStream_t st, int *occupancy_out) {
-    if (P.layout == KP_B_CSR) {
-        SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE);
-        auto kern = csr_pass_kernel<MAXM, MODE, CSR_THREADS>;
-        static int max_dyn = -1;  // once per instantiation, before any stream capture
-        if (max_dyn < 0) {
-            cudaFuncAttributes fa;
-            cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-            if (e != cudaSuccess) return e;
-            const int md = max_optin_smem() - (int)fa.sharedSizeBytes;
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, md);
-            if (e != cudaSuccess) return e;
-            max_dyn = md;
-        }
-        if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
-        if (occupancy_out) {
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, CSR_THREADS, L.total);
-        }
-        kern<<<S.G, CSR_THREADS, L.total, st>>>(P, S, lam, x_bits, round);
-        return cudaGetLastError();
-    } else {
-        int T = dense_tile_users(P);
-        SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, DENSE_THREADS, T, MODE);
-        auto kern = dense_pass_kernel<MAXM, MODE, DENSE_THREADS>;
-        static int max_dyn = -1;  // once per instantiation, before any stream capture
-        if (max_dyn < 0) {
-            cudaFuncAttributes fa;
-            cudaError_t e = cudaFuncGetAttributes(&fa, kern);
-            if (e != cudaSuccess) return e;
-            const int md = max_optin_smem() - (int)fa.sharedSizeBytes;
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, md);
-            if (e != cudaSuccess) return e;
-            max_dyn = md;
-        }
-        if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
-        if (occupancy_out) {
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, DENSE_THREADS, L.total);
-        }
-        kern<<<S.G, DENSE_THREADS, L.total, st>>>(P, S, lam, x_bits, round, T);
-        return cudaGetLastError();
+                     int round, cudaStream_t st, int *occ) {
+    if (P.layout != KP_B_CSR) return launch_dense<MAXM, MODE>(P, S, lam, x_bits, round, st, occ);
+    if constexpr (MAXM <= 16) {
+        if (P.creg == 1) return launch_csr<MAXM, 1, MODE>(P, S, lam, x_bits, round, st, occ);
+        if (P.creg == 2) return launch_csr<MAXM, 2, MODE>(P, S, lam, x_bits, round, st, occ);
     }
+    return launch_csr<MAXM, 0, MODE>(P, S, lam, x_bits, round, st, occ);
 }
 
 template <int MAXM>

@@ -340,6 +340,14 @@ __global__ void validate_kernel(Params P, uint32_t *flags) {
             }
             if (e != e1 || e0 < 0) bad |= 4u;
         }
+        uint32_t cmin = 0xffffffffu, cmax = 0u;
+        for (int64_t q = tid; q < P.N * M; q += stride) {
+            const uint32_t c = P.innz[q];
+            cmin = min(cmin, c);
+            cmax = max(cmax, c);
+        }
+        atomicMin(&flags[3], cmin);
+        atomicMax(&flags[4], cmax);
     }
     for (int64_t k = tid; k < K; k += stride) {
         const double Bk = P.B[k];
