@@ -170,6 +170,30 @@ kp_status kp_dual_backward(kp_problem *h, const double *lambda, const uint32_t *
                            const double *R, const double *upstream, double *grad_lambda,
                            float *grad_p, double *grad_B, void *stream);
 
+/* Allocation-free form of kp_reduce_consumption, for callers that cannot
+ * allocate device memory: a process whose device memory belongs to its own
+ * pool (an outside cudaMalloc would fail or fragment it), or code on a
+ * latency-critical path that must not take the driver's allocation locks.
+ * There is no counterpart in the paper; it computes exactly what
+ * kp_reduce_consumption computes (same kernels), with no handle: the
+ * instance is described by desc at every call and nothing is allocated.
+ *   - Scratch: one file-scope __device__ array of (KP_MAX_K + 5) 64-bit
+ *     words (about 16 KB) per device, kept by every device that loads the
+ *     library until the process exits.  K > KP_MAX_K is rejected
+ *     (KP_EINVAL).
+ *   - The first call on a device looks up the array's device address (once
+ *     per device); make that first call before any stream capture.
+ *   - Each call clears the array, scans the instance as kp_create does
+ *     (KP_EDATA on violations) and waits on `stream` for that scan's result,
+ *     then enqueues the pass and returns; the outputs are valid after the
+ *     stream has been synchronised.
+ *   - Every call shares the array: calls that overlap on the GPU (other
+ *     streams, other host threads) race and must be serialised by the caller.
+ * Arguments and outputs as in kp_create and kp_reduce_consumption. */
+kp_status kp_reduce_consumption_noalloc(const kp_desc *desc, const double *lambda, double *R,
+                                        double *dual_sum, double *primal_sum, double *g,
+                                        uint32_t *x_bits, void *stream);
+
 /* Synchronises the stream and returns the device-side status accumulated by
  * the handle's kernels since the last call (KP_OK, KP_ETIMEOUT or
  * KP_ESTATE), then clears it. */

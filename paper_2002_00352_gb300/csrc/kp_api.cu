@@ -73,6 +73,11 @@ bool check_handle(kp_problem *h) { return h != nullptr && h->P.N > 0; }
 
 }  // namespace
 
+namespace kp {
+// error text for kp_last_error() from entry points defined in other files
+void set_last_error(const char *msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace kp
+
 extern "C" {
 
 const char *kp_last_error(void) { return g_err; }

@@ -110,5 +110,7 @@ cudaError_t launch_backward(const Params &P, const double *lambda, const uint32_
                             float *grad_p, double *grad_B, cudaStream_t st);
 cudaError_t launch_validate(const Params &P, uint32_t *flags, cudaStream_t st);
 cudaError_t launch_shmask(const Params &P, uint32_t *shmask, cudaStream_t st);
+// kp_api.cu
+void set_last_error(const char *msg);
 
 }  // namespace kp

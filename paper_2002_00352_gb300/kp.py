@@ -53,6 +53,7 @@ EXPORTS = [
     "kp_create", "kp_destroy", "kp_solve_users", "kp_reduce_consumption", "kp_dual_value",
     "kp_dd_step", "kp_scd_breakpoints", "kp_threshold_select", "kp_scd_step",
     "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_last_error", "kp_version",
+    "kp_reduce_consumption_noalloc",
 ]
 
 
@@ -75,6 +76,7 @@ def load_library(path: Optional[str] = None):
     lib.kp_dual_backward.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.kp_device_status.argtypes = [P, P]
     lib.kp_select_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
+    lib.kp_reduce_consumption_noalloc.argtypes = [ctypes.POINTER(kp_desc), P, P, P, P, P, P, P]
     lib.kp_last_error.restype = ctypes.c_char_p
     lib.kp_version.restype = ctypes.c_int
     for name in EXPORTS:
@@ -126,6 +128,42 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def _desc(N, M, K, p, B, S, C, b_dense, csr_user_off, csr_item_nnz, csr_val, csr_k):
+    d = kp_desc()
+    d.N, d.M, d.K = int(N), int(M), int(K)
+    d.p = _ptr(p, torch.float32, "p")
+    d.B = _ptr(B, torch.float64, "B")
+    if b_dense is not None:
+        d.b_layout = KP_B_DENSE
+        d.b_dense = _ptr(b_dense, torch.float32, "b_dense")
+    else:
+        d.b_layout = KP_B_CSR
+        d.csr_user_off = _ptr(csr_user_off, torch.int64, "csr_user_off")
+        d.csr_item_nnz = _ptr(csr_item_nnz, torch.uint8, "csr_item_nnz")
+        d.csr_val = _ptr(csr_val, torch.float32, "csr_val")
+        d.csr_k = _ptr(csr_k, torch.int16, "csr_k")
+    Sa = (ctypes.c_uint64 * max(1, len(S)))(*[int(s) for s in S])
+    Ca = (ctypes.c_int32 * max(1, len(C)))(*[int(c) for c in C])
+    d.L = len(S)
+    d.S = ctypes.cast(Sa, ctypes.c_void_p)
+    d.C = ctypes.cast(Ca, ctypes.c_void_p)
+    return d, (Sa, Ca)
+
+
+def kp_reduce_consumption_noalloc(N: int, M: int, K: int, p: torch.Tensor, B: torch.Tensor,
+                                  S: Sequence[int], C: Sequence[int], lam: torch.Tensor,
+                                  b_dense=None, csr_user_off=None, csr_item_nnz=None, csr_val=None,
+                                  csr_k=None, R=None, dual_sum=None, primal_sum=None, g=None,
+                                  x_bits=None, stream=None):
+    """Allocation-free consumption pass (no handle; the instance is described per call)."""
+    d, keep = _desc(N, M, K, p, B, S, C, b_dense, csr_user_off, csr_item_nnz, csr_val, csr_k)
+    _check(load_library().kp_reduce_consumption_noalloc(
+        ctypes.byref(d), _ptr(lam, torch.float64, "lambda"), _ptr(R, torch.float64, "R"),
+        _ptr(dual_sum, torch.float64, "dual_sum"), _ptr(primal_sum, torch.float64, "primal_sum"),
+        _ptr(g, torch.float64, "g"), _ptr(x_bits, None, "x_bits"), _stream(stream)))
+    del keep
 
 
 def kp_create(N: int, M: int, K: int, p: torch.Tensor, B: torch.Tensor, S: Sequence[int],
