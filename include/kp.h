@@ -170,6 +170,38 @@ kp_status kp_dual_backward(kp_problem *h, const double *lambda, const uint32_t *
                            const double *R, const double *upstream, double *grad_lambda,
                            float *grad_p, double *grad_B, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent instances (each its own Eq. (1)-(4) problem, with
+ * its own N, M, K, sets and budgets) solved together.  Every pass over the
+ * users of all instances is one persistent kernel launch over a work list of
+ * (instance, tile of users); the selection runs one block per (instance,
+ * knapsack).  The paper solves one instance at a time; batching is this
+ * library's way to keep the GPU busy with many small ones.
+ *   - Multipliers of the batch: one float64 device array, instance i's K_i
+ *     values at offset koff[i] (kp_batch_layout); same for R.
+ *   - x_bits: instance i's N_i * ceil(M_i/32) words follow instance i-1's.
+ *   - dual_sum / primal_sum: one float64 per instance.
+ *   - Only dense instances (KP_B_DENSE) can be batched (KP_EINVAL otherwise).
+ * Instance data are borrowed as in kp_create; validation as in kp_create.
+ * ------------------------------------------------------------------------ */
+typedef struct kp_batch kp_batch;
+
+kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out);
+kp_status kp_batch_destroy(kp_batch *b);
+/* koff: host int64 [count + 1], offsets of each instance's multipliers. */
+kp_status kp_batch_layout(kp_batch *b, int64_t *koff);
+/* kp_reduce_consumption for every instance (Algorithm 2 Map + Reduce). */
+kp_status kp_batch_reduce_consumption(kp_batch *b, const double *lambda, double *R,
+                                      double *dual_sum, double *primal_sum, uint32_t *x_bits,
+                                      void *stream);
+/* kp_dd_step (Eq. (14)) for every instance with the same alpha. */
+kp_status kp_batch_dd_step(kp_batch *b, const double *lambda, double alpha, double *lambda_next,
+                           void *stream);
+/* kp_scd_step (Algorithms 3-4) for every instance; lambda_next must not alias lambda. */
+kp_status kp_batch_scd_step(kp_batch *b, const double *lambda, double *lambda_next, void *stream);
+/* As kp_device_status, over every instance of the batch. */
+kp_status kp_batch_device_status(kp_batch *b, void *stream);
+
 /* Allocation-free form of kp_reduce_consumption, for callers that cannot
  * allocate device memory: a process whose device memory belongs to its own
  * pool (an outside cudaMalloc would fail or fragment it), or code on a

@@ -19,12 +19,6 @@ namespace kp {
 int pass_grid_size(const Params &P);
 }
 
-struct kp_problem {
-    kp::Params P;
-    kp::Scratch S;
-    int device;
-    std::vector<void *> allocs;
-};
 
 namespace {
 
@@ -84,9 +78,14 @@ const char *kp_last_error(void) { return g_err; }
 
 int kp_version(void) { return 100; }
 
-kp_status kp_create(const kp_desc *d, kp_problem **out) {
-    g_err[0] = 0;
-    if (!d || !out) return fail(KP_EINVAL, "kp_create: NULL argument");
+}  // extern "C"
+
+namespace kp_impl {
+
+// Validates the description and fills h->P (host checks, device scan, fixed-point
+// shifts, CSR shape); allocates nothing that outlives the call.
+kp_status prepare(const kp_desc *d, kp_problem *h) {
+    if (!d) return fail(KP_EINVAL, "NULL description");
     if (d->N < 1) return fail(KP_EINVAL, "N must be >= 1 (got %lld)", (long long)d->N);
     if (d->M < 1 || d->M > KP_MAX_M) return fail(KP_EINVAL, "M must be in 1..%d (got %d)", KP_MAX_M, d->M);
     if (d->K < 1 || d->K > KP_MAX_K) return fail(KP_EINVAL, "K must be in 1..%d (got %d)", KP_MAX_K, d->K);
@@ -116,9 +115,6 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
         }
     int cur_dev = 0;
     KP_CUDA(cudaGetDevice(&cur_dev), "cudaGetDevice");
-
-    kp_problem *h = new (std::nothrow) kp_problem();
-    if (!h) return fail(KP_ENOMEM, "host allocation failed");
     h->device = cur_dev;
     kp::Params &P = h->P;
     P.N = d->N;
@@ -158,7 +154,10 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
     kp_status st = KP_OK;
     // device scan of the instance (Sec. 2 data assumptions)
     uint32_t *flags = nullptr;
-    if ((st = alloc(h, &flags, 5, "validation flags")) != KP_OK) goto fail_out;
+    {
+        cudaError_t ea = cudaMalloc(&flags, 5 * sizeof(uint32_t));
+        if (ea != cudaSuccess) return fail(KP_ENOMEM, "cudaMalloc(validation flags): %s", cudaGetErrorString(ea));
+    }
     {
         const uint32_t init[5] = {0u, 0u, 0u, 0xffffffffu, 0u};
         cudaError_t e0 = cudaMemcpy(flags, init, sizeof(init), cudaMemcpyHostToDevice);
@@ -228,28 +227,40 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
         if (so < 0) so = 0;
         P.fixo = so;
     }
+    P.tile = P.layout == KP_B_DENSE ? kp::dense_tile_users(P) : 0;
+fail_out:
+    cudaFree(flags);
+    return st;
+}
+
+// Allocates the handle's scratch for blocks [g_lo, g_lo + gspan) of a grid of G
+// blocks; budget = breakpoint-buffer entries; ctr = counters owned elsewhere
+// (a batch pools them) or nullptr to allocate.
+kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget,
+                        kp::Counters *ctr) {
+    kp_status st = KP_OK;
+    const kp::Params &P = h->P;
     {
         kp::Scratch &S = h->S;
-        S.G = kp::pass_grid_size(P);
-        const char *env = getenv("KP_BUFFER_ENTRIES");
-        double budget = env ? atof(env) : 4.0 * (double)P.N * P.M;
-        if (!env) {
-            if (budget < (double)(1 << 20)) budget = (double)(1 << 20);
-            if (budget > (double)(1 << 28)) budget = (double)(1 << 28);
-        }
-        long long cap = (long long)(budget / ((double)P.K * S.G));
+        S.G = G;
+        S.g_lo = g_lo;
+        S.gspan = gspan;
+        long long cap = (long long)(budget / ((double)P.K * S.gspan));
         if (cap < 64) cap = 64;
         S.cap_kb = (int)cap;
-        const size_t K = (size_t)P.K, G = (size_t)S.G;
+        const size_t K = (size_t)P.K, GS = (size_t)S.gspan;
         if ((st = alloc(h, &S.Rfix, K, "Rfix")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.objfix, 2, "objective sums")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.reg3, K * 3, "window masses")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.subhist, K * kp::NSUB, "sub-histogram")) != KP_OK) goto fail_out;
-        if ((st = alloc(h, &S.buf, K * G * (size_t)S.cap_kb, "breakpoint buffer")) != KP_OK) goto fail_out;
-        if ((st = alloc(h, &S.bufcnt, K * G, "buffer counts")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.buf, K * GS * (size_t)S.cap_kb, "breakpoint buffer")) != KP_OK) goto fail_out;
+        if ((st = alloc(h, &S.bufcnt, K * GS, "buffer counts")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.ovf, K, "overflow flags")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.sel, K, "selection state")) != KP_OK) goto fail_out;
-        if ((st = alloc(h, &S.ctr, 1, "counters")) != KP_OK) goto fail_out;
+        if (ctr)
+            S.ctr = ctr;
+        else if ((st = alloc(h, &S.ctr, 1, "counters")) != KP_OK)
+            goto fail_out;
         if (P.layout == KP_B_CSR) {
             if ((st = alloc(h, &S.shmask, (size_t)P.N, "shared-entry masks")) != KP_OK) goto fail_out;
             cudaError_t e2 = kp::launch_shmask(P, S.shmask, 0);
@@ -270,12 +281,37 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
             goto fail_out;
         }
     }
+fail_out:
+    return st;
+}
+
+}  // namespace kp_impl
+
+extern "C" {
+
+kp_status kp_create(const kp_desc *d, kp_problem **out) {
+    g_err[0] = 0;
+    if (!d || !out) return fail(KP_EINVAL, "kp_create: NULL argument");
+    kp_problem *h = new (std::nothrow) kp_problem();
+    if (!h) return fail(KP_ENOMEM, "host allocation failed");
+    kp_status st = kp_impl::prepare(d, h);
+    if (st == KP_OK) {
+        const char *env = getenv("KP_BUFFER_ENTRIES");
+        double budget = env ? atof(env) : 4.0 * (double)h->P.N * h->P.M;
+        if (!env) {
+            if (budget < (double)(1 << 20)) budget = (double)(1 << 20);
+            if (budget > (double)(1 << 28)) budget = (double)(1 << 28);
+        }
+        const int G = kp::pass_grid_size(h->P);
+        st = kp_impl::alloc_scratch(h, G, 0, G, budget, nullptr);
+    }
+    if (st != KP_OK) {
+        free_all(h);
+        delete h;
+        return st;
+    }
     *out = h;
     return KP_OK;
-fail_out:
-    free_all(h);
-    delete h;
-    return st;
 }
 
 kp_status kp_destroy(kp_problem *h) {

@@ -1,0 +1,237 @@
+// kp_batch.cu -- many independent instances of the problem solved together:
+// every pass over the users of all instances is one persistent launch over a
+// work list of (instance, tile of users); the selection kernels run one block
+// per (instance, knapsack).  Each instance keeps its own parameters, scratch,
+// multipliers and counters; only the launches are shared.
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kp_internal.h"
+
+struct kp_batch {
+    int count = 0;
+    std::vector<kp_problem *> probs;
+    int maxm = 64;
+    int G = 0;
+    size_t smem[3] = {0, 0, 0};
+    int64_t totK = 0, ntiles = 0;
+    kp::BatchDev B{};
+    kp::Counters *ctr = nullptr;
+    std::vector<void *> allocs;
+    std::vector<int64_t> koff;
+};
+
+namespace {
+
+kp_status bfail(kp_status s, const char *msg, cudaError_t e = cudaSuccess) {
+    char buf[320];
+    if (e != cudaSuccess)
+        snprintf(buf, sizeof(buf), "%s: %s", msg, cudaGetErrorString(e));
+    else
+        snprintf(buf, sizeof(buf), "%s", msg);
+    kp::set_last_error(buf);
+    return s;
+}
+
+template <class T>
+kp_status bcopy(kp_batch *b, T **dst, const std::vector<T> &src, const char *what) {
+    void *p = nullptr;
+    const size_t bytes = std::max<size_t>(sizeof(T), src.size() * sizeof(T));
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return bfail(KP_ENOMEM, what, e);
+    b->allocs.push_back(p);
+    if (!src.empty()) e = cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bfail(KP_ECUDA, what, e);
+    *dst = static_cast<T *>(p);
+    return KP_OK;
+}
+
+void destroy(kp_batch *b) {
+    for (kp_problem *h : b->probs)
+        if (h) kp_destroy(h);
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+int maxm_class(int M) { return M <= 8 ? 8 : (M <= 10 ? 10 : (M <= 16 ? 16 : 64)); }
+
+}  // namespace
+
+extern "C" {
+
+kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out) {
+    if (!descs || !out || count < 1) return bfail(KP_EINVAL, "kp_batch_create: NULL argument or count < 1");
+    kp_batch *b = new (std::nothrow) kp_batch();
+    if (!b) return bfail(KP_ENOMEM, "host allocation failed");
+    b->count = count;
+    b->probs.assign(count, nullptr);
+    kp_status st = KP_OK;
+    int maxM = 1;
+    // parameters of every instance (validation and data scan as in kp_create)
+    for (int i = 0; i < count && st == KP_OK; ++i) {
+        if (descs[i].b_layout != KP_B_DENSE) {
+            st = bfail(KP_EINVAL, "kp_batch_create: only dense instances can be batched");
+            break;
+        }
+        b->probs[i] = new (std::nothrow) kp_problem();
+        if (!b->probs[i]) {
+            st = bfail(KP_ENOMEM, "host allocation failed");
+            break;
+        }
+        st = kp_impl::prepare(&descs[i], b->probs[i]);
+        maxM = std::max(maxM, (int)descs[i].M);
+    }
+    if (st != KP_OK) {
+        destroy(b);
+        return st;
+    }
+    b->maxm = maxm_class(maxM);
+    for (int m = 0; m < 3; ++m)
+        for (int i = 0; i < count; ++i) b->smem[m] = std::max(b->smem[m], kp::dense_smem_bytes(b->probs[i]->P, m));
+    b->G = kp::batch_grid_size(b->maxm, b->smem[kp::MODE_HIST]);
+    if (b->G < 1) {
+        destroy(b);
+        return bfail(KP_ECUDA, "kp_batch_create: no resident block fits the shared memory of the batch");
+    }
+    // work list: tiles of every instance, in instance order
+    std::vector<int32_t> tile_inst;
+    std::vector<int64_t> tile_u0, xoff(count);
+    std::vector<int64_t> tstart(count), tend(count);
+    b->koff.assign(count + 1, 0);
+    int64_t xo = 0;
+    for (int i = 0; i < count; ++i) {
+        const kp::Params &P = b->probs[i]->P;
+        tstart[i] = (int64_t)tile_inst.size();
+        for (int64_t u0 = 0; u0 < P.N; u0 += P.tile) {
+            tile_inst.push_back(i);
+            tile_u0.push_back(u0);
+        }
+        tend[i] = (int64_t)tile_inst.size();
+        b->koff[i + 1] = b->koff[i] + P.K;
+        xoff[i] = xo;
+        xo += P.N * P.W;
+    }
+    b->ntiles = (int64_t)tile_inst.size();
+    b->totK = b->koff[count];
+    const int64_t per = (b->ntiles + b->G - 1) / b->G;
+    std::vector<int32_t> kinst(b->totK);
+    for (int i = 0; i < count; ++i)
+        for (int64_t k = b->koff[i]; k < b->koff[i + 1]; ++k) kinst[k] = i;
+    {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, sizeof(kp::Counters) * count);
+        if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof(kp::Counters) * count);
+        if (e != cudaSuccess) {
+            destroy(b);
+            return bfail(KP_ENOMEM, "batch counters", e);
+        }
+        b->allocs.push_back(p);
+        b->ctr = static_cast<kp::Counters *>(p);
+    }
+    std::vector<kp::Params> hP(count);
+    std::vector<kp::Scratch> hS(count);
+    for (int i = 0; i < count && st == KP_OK; ++i) {
+        kp_problem *h = b->probs[i];
+        const int g_lo = (int)(tstart[i] / per), g_hi = (int)((tend[i] - 1) / per);
+        double budget = 4.0 * (double)h->P.N * h->P.M;
+        budget = std::min(std::max(budget, (double)(1 << 16)), (double)(1 << 24));
+        st = kp_impl::alloc_scratch(h, b->G, g_lo, g_hi - g_lo + 1, budget, b->ctr + i);
+        hP[i] = h->P;
+        hS[i] = h->S;
+    }
+    if (st == KP_OK) st = bcopy(b, const_cast<kp::Params **>(&b->B.P), hP, "batch parameters");
+    if (st == KP_OK) st = bcopy(b, &b->B.S, hS, "batch scratch descriptors");
+    if (st == KP_OK) st = bcopy(b, const_cast<int64_t **>(&b->B.koff), b->koff, "batch offsets");
+    if (st == KP_OK) st = bcopy(b, const_cast<int64_t **>(&b->B.xoff), xoff, "batch x offsets");
+    if (st == KP_OK) st = bcopy(b, const_cast<int32_t **>(&b->B.kinst), kinst, "batch knapsack table");
+    if (st == KP_OK) st = bcopy(b, const_cast<int32_t **>(&b->B.tile_inst), tile_inst, "batch tiles");
+    if (st == KP_OK) st = bcopy(b, const_cast<int64_t **>(&b->B.tile_u0), tile_u0, "batch tiles");
+    if (st != KP_OK) {
+        destroy(b);
+        return st;
+    }
+    b->B.ntiles = b->ntiles;
+    b->B.count = count;
+    *out = b;
+    return KP_OK;
+}
+
+kp_status kp_batch_destroy(kp_batch *b) {
+    if (!b) return KP_OK;
+    cudaDeviceSynchronize();
+    destroy(b);
+    return KP_OK;
+}
+
+kp_status kp_batch_layout(kp_batch *b, int64_t *koff) {
+    if (!b || !koff) return bfail(KP_EINVAL, "kp_batch_layout: NULL argument");
+    for (int i = 0; i <= b->count; ++i) koff[i] = b->koff[i];
+    return KP_OK;
+}
+
+kp_status kp_batch_reduce_consumption(kp_batch *b, const double *lambda, double *R, double *dual_sum,
+                                      double *primal_sum, uint32_t *x_bits, void *stream) {
+    if (!b || !lambda) return bfail(KP_EINVAL, "kp_batch_reduce_consumption: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_STATE], b->G, lambda,
+                                          kp::MODE_STATE, 0, x_bits, st);
+    if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, R, dual_sum, primal_sum, 0.0, nullptr, st);
+    if (e != cudaSuccess) return bfail(KP_ECUDA, "batch consumption pass", e);
+    return KP_OK;
+}
+
+kp_status kp_batch_dd_step(kp_batch *b, const double *lambda, double alpha, double *lambda_next,
+                           void *stream) {
+    if (!b || !lambda || !lambda_next) return bfail(KP_EINVAL, "kp_batch_dd_step: NULL argument");
+    if (!(alpha >= 0.0)) return bfail(KP_EINVAL, "kp_batch_dd_step: alpha must be >= 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_STATE], b->G, lambda,
+                                          kp::MODE_STATE, 0, nullptr, st);
+    if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, nullptr, nullptr, nullptr, alpha, lambda_next, st);
+    if (e != cudaSuccess) return bfail(KP_ECUDA, "batch dual-descent step", e);
+    return KP_OK;
+}
+
+kp_status kp_batch_scd_step(kp_batch *b, const double *lambda, double *lambda_next, void *stream) {
+    if (!b || !lambda || !lambda_next) return bfail(KP_EINVAL, "kp_batch_scd_step: NULL argument");
+    if (lambda == lambda_next) return bfail(KP_EINVAL, "kp_batch_scd_step: lambda_next must not alias lambda");
+    cudaStream_t st = (cudaStream_t)stream;
+    // clear every instance's counters except its status word
+    cudaError_t e = cudaMemset2DAsync(b->ctr, sizeof(kp::Counters), 0, offsetof(kp::Counters, status),
+                                      (size_t)b->count, st);
+    if (e == cudaSuccess)
+        e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_HIST], b->G, lambda, kp::MODE_HIST, 0,
+                                  nullptr, st);
+    if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, nullptr, nullptr, nullptr, 0.0, nullptr, st);
+    if (e == cudaSuccess) e = kp::launch_batch_select(b->B, b->totK, lambda, lambda_next, 0, st);
+    for (int r = 1; r <= kp::MAX_REFINE && e == cudaSuccess; ++r) {
+        e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_REFINE], b->G, lambda, kp::MODE_REFINE, r,
+                                  nullptr, st);
+        if (e == cudaSuccess) e = kp::launch_batch_select(b->B, b->totK, lambda, lambda_next, r, st);
+    }
+    if (e != cudaSuccess) return bfail(KP_ECUDA, "batch SCD step", e);
+    return KP_OK;
+}
+
+kp_status kp_batch_device_status(kp_batch *b, void *stream) {
+    if (!b) return bfail(KP_EINVAL, "kp_batch_device_status: NULL batch");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    std::vector<kp::Counters> h(b->count);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), b->ctr, sizeof(kp::Counters) * b->count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bfail(KP_ECUDA, "kp_batch_device_status", e);
+    int32_t status = 0;
+    for (const auto &c : h) status |= c.status;
+    if (status) {
+        e = cudaMemset2D(reinterpret_cast<char *>(b->ctr) + offsetof(kp::Counters, status), sizeof(kp::Counters), 0,
+                         sizeof(int32_t), (size_t)b->count);
+        if (e != cudaSuccess) return bfail(KP_ECUDA, "kp_batch_device_status", e);
+    }
+    if (status & (1 << KP_ETIMEOUT)) return bfail(KP_ETIMEOUT, "a kernel's bounded wait ran out");
+    if (status & (1 << KP_ESTATE)) return bfail(KP_ESTATE, "threshold selection did not converge");
+    return KP_OK;
+}
+
+}  // extern "C"

@@ -2,6 +2,8 @@
 // kernels.  Not part of the public interface (include/kp.h is).
 #pragma once
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/kp.h"
@@ -67,6 +69,7 @@ struct Params {
     const double *B;
     int32_t fixs;              // fixed-point shift of b sums: units of 2^-fixs
     int32_t fixo;              // fixed-point shift of the objective sums
+    int32_t tile;              // dense: users per shared-memory tile
     int32_t creg;              // CSR: every item has exactly creg entries (0: not regular)
     int32_t vec;               // CSR regular rows aligned for vector loads (M in {8, 10, 16})
     int64_t uoff0;             // csr_user_off[0]
@@ -76,13 +79,14 @@ struct Params {
 // device scratch owned by a handle
 struct Scratch {
     int32_t G;                        // persistent grid size of the user pass
+    int32_t g_lo, gspan;              // blocks [g_lo, g_lo + gspan) can touch this instance
     int32_t cap_kb;                   // buffer entries per (k, block)
     unsigned long long *Rfix;         // [K]
     unsigned long long *objfix;       // [2] fixed-point dual and primal sums
     unsigned long long *reg3;         // [K][3] mass at/above, inside, below the window
     unsigned long long *subhist;      // [K][NSUB]
-    uint2 *buf;                       // [K][G][cap_kb] (key, float bits of v2)
-    uint32_t *bufcnt;                 // [K][G]
+    uint2 *buf;                       // [K][gspan][cap_kb] (key, float bits of v2)
+    uint32_t *bufcnt;                 // [K][gspan]
     uint32_t *ovf;                    // [K]
     SelK *sel;                        // [K]
     Counters *ctr;
@@ -90,6 +94,20 @@ struct Scratch {
 };
 
 enum PassMode { MODE_STATE = 0, MODE_HIST = 1, MODE_REFINE = 2 };
+
+// Many independent instances processed by one persistent launch: the tile
+// list is ordered by instance; block b takes tiles [b * per, (b + 1) * per).
+struct BatchDev {
+    const Params *P;        // [count]
+    Scratch *S;             // [count]
+    const int64_t *koff;    // [count + 1] offsets of each instance's multipliers
+    const int64_t *xoff;    // [count] offsets of each instance's x words
+    const int32_t *kinst;   // [sum K] instance of every global knapsack index
+    const int32_t *tile_inst;  // [ntiles]
+    const int64_t *tile_u0;    // [ntiles]
+    int64_t ntiles;
+    int32_t count;
+};
 
 struct PassOut {
     uint32_t *x_bits;  // optional
@@ -105,6 +123,15 @@ cudaError_t launch_finalize(const Params &P, const Scratch &S, const double *lam
                             double *lambda_next, cudaStream_t st);
 cudaError_t launch_select(const Params &P, const Scratch &S, const double *lambda,
                           double *lambda_next, int round, cudaStream_t st);
+cudaError_t launch_batch_pass(const BatchDev &B, int maxm, size_t smem, int grid, const double *lam,
+                              int mode, int round, uint32_t *x_all, cudaStream_t st);
+int batch_grid_size(int maxm, size_t smem);
+size_t dense_smem_bytes(const Params &P, int mode);
+int dense_tile_users(const Params &P);
+cudaError_t launch_batch_finalize(const BatchDev &B, const double *lam, double *R, double *dual,
+                                  double *primal, double alpha, double *lam_next, cudaStream_t st);
+cudaError_t launch_batch_select(const BatchDev &B, int64_t totK, const double *lam,
+                                double *lam_next, int round, cudaStream_t st);
 cudaError_t launch_backward(const Params &P, const double *lambda, const uint32_t *x_bits,
                             const double *R, const double *upstream, double *grad_lambda,
                             float *grad_p, double *grad_B, cudaStream_t st);
@@ -114,3 +141,17 @@ cudaError_t launch_shmask(const Params &P, uint32_t *shmask, cudaStream_t st);
 void set_last_error(const char *msg);
 
 }  // namespace kp
+
+// a problem handle (include/kp.h): parameters, scratch, and the allocations to free
+struct kp_problem {
+    kp::Params P;
+    kp::Scratch S;
+    int device;
+    std::vector<void *> allocs;
+};
+
+namespace kp_impl {
+// kp_api.cu: validation + parameters, and scratch for blocks [g_lo, g_lo + gspan)
+kp_status prepare(const kp_desc *d, kp_problem *h);
+kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget, kp::Counters *ctr);
+}  // namespace kp_impl

@@ -173,6 +173,8 @@ kp_status kp_reduce_consumption_noalloc(const kp_desc *d, const double *lambda, 
     kp::Scratch S;
     memset(&S, 0, sizeof(S));
     S.G = kp::pass_grid_size(P);
+    S.g_lo = 0;
+    S.gspan = S.G;
     S.Rfix = Rfix;
     S.objfix = objfix;
     e = kp::launch_user_pass(P, S, lambda, kp::MODE_STATE, 0, x_bits, st);

@@ -85,7 +85,7 @@ __device__ __forceinline__ int bitlen(uint32_t x) { return x ? 32 - __clz(x) : 0
 template <int MODE>
 __device__ __forceinline__ void init_block_state(const Params &P, const Scratch &S,
                                                  const double *lam, const SmemLayout &L,
-                                                 unsigned char *smem, int round) {
+                                                 unsigned char *smem, int round, bool leader) {
     const int K = P.K;
     float *lamf = (float *)(smem + L.lamf);
     uint32_t *ckey = (uint32_t *)(smem + L.ckey);
@@ -114,7 +114,7 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
             const uint32_t whi = wh > (long long)KEY_INF ? KEY_INF : (uint32_t)wh;
             ckey[k] = c;
             wwin[k] = sk.w;
-            if (blockIdx.x == 0) {
+            if (leader) {
                 S.sel[k].ckey = c;
                 S.sel[k].wlo = wlo;
                 S.sel[k].whi = whi;
@@ -156,7 +156,7 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
         if (MODE != MODE_REFINE && rfix[k]) atomicAdd(&S.Rfix[k], rfix[k]);
         if (MODE != MODE_STATE) {
             uint32_t c = bcnt[k];
-            S.bufcnt[(size_t)k * S.G + blockIdx.x] = c < (uint32_t)S.cap_kb ? c : (uint32_t)S.cap_kb;
+            S.bufcnt[(size_t)k * S.gspan + (blockIdx.x - S.g_lo)] = c < (uint32_t)S.cap_kb ? c : (uint32_t)S.cap_kb;
             if (c > (uint32_t)S.cap_kb) S.ovf[k] = 1u;
         }
     }
@@ -186,8 +186,8 @@ __device__ __forceinline__ WindowSink make_window_sink(const Params &P, const Sc
     ws.bcnt = (uint32_t *)(smem + L.bcnt);
     ws.buf = S.buf;
     ws.cap_kb = S.cap_kb;
-    ws.G = S.G;
-    ws.blk = blockIdx.x;
+    ws.G = S.gspan;
+    ws.blk = blockIdx.x - S.g_lo;
     ws.fixs = P.fixs;
     return ws;
 }
@@ -202,8 +202,8 @@ __device__ __forceinline__ RefineSink make_refine_sink(const Params &P, const Sc
     rs.bcnt = (uint32_t *)(smem + L.bcnt);
     rs.buf = S.buf;
     rs.cap_kb = S.cap_kb;
-    rs.G = S.G;
-    rs.blk = blockIdx.x;
+    rs.G = S.gspan;
+    rs.blk = blockIdx.x - S.g_lo;
     rs.fixs = P.fixs;
     return rs;
 }
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch 
     if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
     if (MODE != MODE_STATE && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&S.ctr->stats[0], 1ull);
     const SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, THREADS, 0, MODE);
-    init_block_state<MODE>(P, S, lam, L, smem, round);
+    init_block_state<MODE>(P, S, lam, L, smem, round, blockIdx.x == 0);
     __syncthreads();
     unsigned long long dsum = 0ull, psum = 0ull;
     if (MODE == MODE_HIST) {
@@ -798,127 +798,180 @@ __global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch 
 // computed per (user, item), the greedy per user, and consumption and the
 // breakpoints per (user, knapsack).
 // ------------------------------------------------------------------------------------------
+// One tile of nu users starting at u0 (T users per tile): stage, reduce,
+// Algorithm 1, then consumption and Algorithm 4's Map per (user, knapsack).
 template <int MAXM, int MODE, int THREADS>
-__global__ void __launch_bounds__(THREADS) dense_pass_kernel(Params P, Scratch S, const double *lam,
-                                                             uint32_t *x_bits, int round, int T) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
-    if (MODE != MODE_STATE && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&S.ctr->stats[0], 1ull);
+__device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, const SmemLayout &L,
+                                           unsigned char *smem, int64_t u0, int nu, int T,
+                                           uint32_t *x_bits, unsigned long long &dsum,
+                                           unsigned long long &psum) {
     const int M = P.M, K = P.K;
-    const SmemLayout L = smem_layout(KP_B_DENSE, K, M, MAXM, THREADS, T, MODE);
-    init_block_state<MODE>(P, S, lam, L, smem, round);
-    __syncthreads();
     const float *lamf = (const float *)(smem + L.lamf);
     unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
     float *tp = (float *)(smem + L.tile_p);
     float *tb = (float *)(smem + L.tile_b);
     float *pt = (float *)(smem + L.rows);
     uint64_t *selm = (uint64_t *)(smem + L.selm);
-    unsigned long long dsum = 0ull, psum = 0ull;
-
     const bool b_al = ((reinterpret_cast<uintptr_t>(P.b) & 15u) == 0) && ((M * K) % 4 == 0 || T % 4 == 0);
     const bool p_al = ((reinterpret_cast<uintptr_t>(P.p) & 15u) == 0) && ((M % 4) == 0 || T % 4 == 0);
+    // stage the tile
+    {
+        const size_t nb = (size_t)nu * M * K;
+        const float *src = P.b + (size_t)u0 * M * K;
+        if (b_al) {
+            const size_t n4 = nb >> 2;
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+            float4 *d4 = reinterpret_cast<float4 *>(tb);
+            for (size_t q = threadIdx.x; q < n4; q += THREADS) d4[q] = __ldg(s4 + q);
+            for (size_t q = (n4 << 2) + threadIdx.x; q < nb; q += THREADS) tb[q] = __ldg(src + q);
+        } else {
+            for (size_t q = threadIdx.x; q < nb; q += THREADS) tb[q] = __ldg(src + q);
+        }
+        const size_t npn = (size_t)nu * M;
+        const float *ps = P.p + (size_t)u0 * M;
+        if (p_al) {
+            const size_t n4 = npn >> 2;
+            const float4 *s4 = reinterpret_cast<const float4 *>(ps);
+            float4 *d4 = reinterpret_cast<float4 *>(tp);
+            for (size_t q = threadIdx.x; q < n4; q += THREADS) d4[q] = __ldg(s4 + q);
+            for (size_t q = (n4 << 2) + threadIdx.x; q < npn; q += THREADS) tp[q] = __ldg(ps + q);
+        } else {
+            for (size_t q = threadIdx.x; q < npn; q += THREADS) tp[q] = __ldg(ps + q);
+        }
+    }
+    __syncthreads();
+    // Sec. 4.2 reduced costs, four partial sums per item
+    for (int idx = threadIdx.x; idx < nu * M; idx += THREADS) {
+        const float *br = tb + (size_t)idx * K;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int k = 0;
+        for (; k + 3 < K; k += 4) {
+            a0 = fmaf(lamf[k], br[k], a0);
+            a1 = fmaf(lamf[k + 1], br[k + 1], a1);
+            a2 = fmaf(lamf[k + 2], br[k + 2], a2);
+            a3 = fmaf(lamf[k + 3], br[k + 3], a3);
+        }
+        for (; k < K; ++k) a0 = fmaf(lamf[k], br[k], a0);
+        pt[idx] = tp[idx] - ((a0 + a1) + (a2 + a3));
+    }
+    __syncthreads();
+    // Algorithm 1 per user
+    for (int u = threadIdx.x; u < nu; u += THREADS) {
+        const float *ptu = pt + (size_t)u * M;
+        uint64_t pos = 0;
+        for (int j = 0; j < M; ++j)
+            if (ptu[j] > 0.f) pos |= 1ull << j;
+        Walk w;
+        greedy_walk(ptu, 1, pos, P.tree, w);
+        selm[u] = w.sel;
+        if (MODE != MODE_REFINE) {
+            const int64_t i = u0 + u;
+            if (x_bits)
+                for (int q = 0; q < P.W; ++q) x_bits[(size_t)i * P.W + q] = (uint32_t)(w.sel >> (32 * q));
+            uint64_t r = w.sel;
+            float du = 0.f, pu = 0.f;
+            while (r) {
+                int j = __ffsll((long long)r) - 1;
+                r &= r - 1;
+                du += ptu[j];
+                pu += tp[(size_t)u * M + j];
+            }
+            dsum += fixmass(du, P.fixo);
+            psum += fixmass(pu, P.fixo);
+        }
+    }
+    __syncthreads();
+    // per (user, knapsack): consumption and Algorithm 4's Map
+    for (int idx = threadIdx.x; idx < nu * K; idx += THREADS) {
+        const int u = idx / K, k = idx - u * K;
+        const float *bcol = tb + (size_t)u * M * K + k;
+        if (MODE != MODE_REFINE) {
+            uint64_t r = selm[u];
+            unsigned long long acc = 0ull;
+            while (r) {
+                int j = __ffsll((long long)r) - 1;
+                r &= r - 1;
+                acc += fixmass(bcol[(size_t)j * K], P.fixs);
+            }
+            if (acc) shared_add_u64(&rfix[k], acc);
+        }
+        if (MODE != MODE_STATE) {
+            uint64_t J = 0;
+            for (int j = 0; j < M; ++j)
+                if (bcol[(size_t)j * K] > 0.f) J |= 1ull << j;
+            if (MODE == MODE_HIST) {
+                WindowSink ws = make_window_sink(P, S, L, smem);
+                sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, ws);
+            } else {
+                RefineSink rs = make_refine_sink(P, S, L, smem);
+                sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, rs);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int MAXM, int MODE, int THREADS>
+__global__ void __launch_bounds__(THREADS) dense_pass_kernel(Params P, Scratch S, const double *lam,
+                                                             uint32_t *x_bits, int round, int T) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
+    if (MODE != MODE_STATE && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&S.ctr->stats[0], 1ull);
+    const SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, THREADS, T, MODE);
+    init_block_state<MODE>(P, S, lam, L, smem, round, blockIdx.x == 0);
+    __syncthreads();
+    unsigned long long dsum = 0ull, psum = 0ull;
     const int64_t ntiles = (P.N + T - 1) / T;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t u0 = tile * T;
         const int nu = (int)((P.N - u0) < T ? (P.N - u0) : T);
-        // stage the tile
-        {
-            const size_t nb = (size_t)nu * M * K;
-            const float *src = P.b + (size_t)u0 * M * K;
-            if (b_al) {
-                const size_t n4 = nb >> 2;
-                const float4 *s4 = reinterpret_cast<const float4 *>(src);
-                float4 *d4 = reinterpret_cast<float4 *>(tb);
-                for (size_t q = threadIdx.x; q < n4; q += THREADS) d4[q] = __ldg(s4 + q);
-                for (size_t q = (n4 << 2) + threadIdx.x; q < nb; q += THREADS) tb[q] = __ldg(src + q);
-            } else {
-                for (size_t q = threadIdx.x; q < nb; q += THREADS) tb[q] = __ldg(src + q);
-            }
-            const size_t npn = (size_t)nu * M;
-            const float *ps = P.p + (size_t)u0 * M;
-            if (p_al) {
-                const size_t n4 = npn >> 2;
-                const float4 *s4 = reinterpret_cast<const float4 *>(ps);
-                float4 *d4 = reinterpret_cast<float4 *>(tp);
-                for (size_t q = threadIdx.x; q < n4; q += THREADS) d4[q] = __ldg(s4 + q);
-                for (size_t q = (n4 << 2) + threadIdx.x; q < npn; q += THREADS) tp[q] = __ldg(ps + q);
-            } else {
-                for (size_t q = threadIdx.x; q < npn; q += THREADS) tp[q] = __ldg(ps + q);
-            }
-        }
-        __syncthreads();
-        // Sec. 4.2 reduced costs, four partial sums per item
-        for (int idx = threadIdx.x; idx < nu * M; idx += THREADS) {
-            const float *br = tb + (size_t)idx * K;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-            int k = 0;
-            for (; k + 3 < K; k += 4) {
-                a0 = fmaf(lamf[k], br[k], a0);
-                a1 = fmaf(lamf[k + 1], br[k + 1], a1);
-                a2 = fmaf(lamf[k + 2], br[k + 2], a2);
-                a3 = fmaf(lamf[k + 3], br[k + 3], a3);
-            }
-            for (; k < K; ++k) a0 = fmaf(lamf[k], br[k], a0);
-            pt[idx] = tp[idx] - ((a0 + a1) + (a2 + a3));
-        }
-        __syncthreads();
-        // Algorithm 1 per user
-        for (int u = threadIdx.x; u < nu; u += THREADS) {
-            const float *ptu = pt + (size_t)u * M;
-            uint64_t pos = 0;
-            for (int j = 0; j < M; ++j)
-                if (ptu[j] > 0.f) pos |= 1ull << j;
-            Walk w;
-            greedy_walk(ptu, 1, pos, P.tree, w);
-            selm[u] = w.sel;
-            if (MODE != MODE_REFINE) {
-                const int64_t i = u0 + u;
-                if (x_bits)
-                    for (int q = 0; q < P.W; ++q) x_bits[(size_t)i * P.W + q] = (uint32_t)(w.sel >> (32 * q));
-                uint64_t r = w.sel;
-                float du = 0.f, pu = 0.f;
-                while (r) {
-                    int j = __ffsll((long long)r) - 1;
-                    r &= r - 1;
-                    du += ptu[j];
-                    pu += tp[(size_t)u * M + j];
-                }
-                dsum += fixmass(du, P.fixo);
-                psum += fixmass(pu, P.fixo);
-            }
-        }
-        __syncthreads();
-        // per (user, knapsack): consumption and Algorithm 4's Map
-        for (int idx = threadIdx.x; idx < nu * K; idx += THREADS) {
-            const int u = idx / K, k = idx - u * K;
-            const float *bcol = tb + (size_t)u * M * K + k;
-            if (MODE != MODE_REFINE) {
-                uint64_t r = selm[u];
-                unsigned long long acc = 0ull;
-                while (r) {
-                    int j = __ffsll((long long)r) - 1;
-                    r &= r - 1;
-                    acc += fixmass(bcol[(size_t)j * K], P.fixs);
-                }
-                if (acc) shared_add_u64(&rfix[k], acc);
-            }
-            if (MODE != MODE_STATE) {
-                uint64_t J = 0;
-                for (int j = 0; j < M; ++j)
-                    if (bcol[(size_t)j * K] > 0.f) J |= 1ull << j;
-                if (MODE == MODE_HIST) {
-                    WindowSink ws = make_window_sink(P, S, L, smem);
-                    sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, ws);
-                } else {
-                    RefineSink rs = make_refine_sink(P, S, L, smem);
-                    sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, rs);
-                }
-            }
-        }
-        __syncthreads();
+        dense_tile<MAXM, MODE, THREADS>(P, S, L, smem, u0, nu, T, x_bits, dsum, psum);
     }
     flush_block_state<MODE>(P, S, L, smem, dsum, psum);
+}
+
+// Batched pass: one persistent launch over the tiles of many dense instances.
+// The tile list is ordered by instance and every block takes a contiguous
+// range of it, so a block switches instance rarely; at a switch it flushes the
+// previous instance's block state into that instance's scratch and loads the
+// next instance's parameters and multipliers.
+template <int MAXM, int MODE, int THREADS>
+__global__ void __launch_bounds__(THREADS) dense_batch_kernel(BatchDev B, const double *lam_all,
+                                                              uint32_t *x_all, int round) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Params sP;
+    __shared__ Scratch sS;
+    __shared__ int s_skip;
+    const int64_t per = (B.ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * per;
+    const int64_t t1 = t0 + per < B.ntiles ? t0 + per : B.ntiles;
+    int cur = -1;
+    unsigned long long dsum = 0ull, psum = 0ull;
+    SmemLayout L;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int inst = B.tile_inst[t];
+        if (inst != cur) {
+            if (cur >= 0 && !s_skip) flush_block_state<MODE>(sP, sS, L, smem, dsum, psum);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                sP = B.P[inst];
+                sS = B.S[inst];
+                s_skip = MODE == MODE_REFINE && sS.ctr->n_unres[round] == 0;
+            }
+            __syncthreads();
+            cur = inst;
+            dsum = psum = 0ull;
+            L = smem_layout(KP_B_DENSE, sP.K, sP.M, MAXM, THREADS, sP.tile, MODE);
+            if (!s_skip) init_block_state<MODE>(sP, sS, lam_all + B.koff[inst], L, smem, round, t == 0 || B.tile_inst[t - 1] != inst);
+            __syncthreads();
+        }
+        if (s_skip) continue;
+        const int64_t u0 = B.tile_u0[t];
+        const int nu = (int)((sP.N - u0) < sP.tile ? (sP.N - u0) : sP.tile);
+        dense_tile<MAXM, MODE, THREADS>(sP, sS, L, smem, u0, nu, sP.tile,
+                                        x_all ? x_all + B.xoff[inst] : nullptr, dsum, psum);
+    }
+    if (cur >= 0 && !s_skip) flush_block_state<MODE>(sP, sS, L, smem, dsum, psum);
 }
 
 int max_optin_smem() {
@@ -935,14 +988,6 @@ int max_optin_smem() {
 constexpr int CSR_THREADS = 512;
 constexpr int DENSE_THREADS = 256;
 
-int dense_tile_users(const Params &P) {
-    long long per = (long long)P.M * P.K * 4;
-    long long T = DENSE_TILE_BYTES / per;
-    if (T > 256) T = 256;
-    if (T >= 4) T &= ~3LL;
-    if (T < 1) T = 1;
-    return (int)T;
-}
 
 template <class Kern>
 cudaError_t prepare_kernel(Kern kern, int *max_dyn) {
@@ -1017,7 +1062,77 @@ cudaError_t dispatch(const Params &P, const Scratch &S, const double *lam, int m
     return launch_m<64>(P, S, lam, mode, round, x_bits, st, occ);
 }
 
+template <int MAXM, int MODE>
+cudaError_t launch_batch_t(const BatchDev &B, size_t smem, int grid, const double *lam, int round,
+                           uint32_t *x_all, cudaStream_t st, int *occupancy_out) {
+    auto kern = dense_batch_kernel<MAXM, MODE, DENSE_THREADS>;
+    static int max_dyn = -1;
+    cudaError_t e = prepare_kernel(kern, &max_dyn);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
+    if (occupancy_out)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, DENSE_THREADS, smem);
+    kern<<<grid, DENSE_THREADS, smem, st>>>(B, lam, x_all, round);
+    return cudaGetLastError();
+}
+
+template <int MAXM>
+cudaError_t launch_batch_m(const BatchDev &B, size_t smem, int grid, const double *lam, int mode,
+                           int round, uint32_t *x_all, cudaStream_t st, int *occ) {
+    switch (mode) {
+        case MODE_STATE: return launch_batch_t<MAXM, MODE_STATE>(B, smem, grid, lam, round, x_all, st, occ);
+        case MODE_HIST: return launch_batch_t<MAXM, MODE_HIST>(B, smem, grid, lam, round, x_all, st, occ);
+        default: return launch_batch_t<MAXM, MODE_REFINE>(B, smem, grid, lam, round, x_all, st, occ);
+    }
+}
+
+cudaError_t batch_dispatch(const BatchDev &B, int maxm, size_t smem, int grid, const double *lam, int mode,
+                           int round, uint32_t *x_all, cudaStream_t st, int *occ) {
+    if (maxm <= 8) return launch_batch_m<8>(B, smem, grid, lam, mode, round, x_all, st, occ);
+    if (maxm <= 10) return launch_batch_m<10>(B, smem, grid, lam, mode, round, x_all, st, occ);
+    if (maxm <= 16) return launch_batch_m<16>(B, smem, grid, lam, mode, round, x_all, st, occ);
+    return launch_batch_m<64>(B, smem, grid, lam, mode, round, x_all, st, occ);
+}
+
 }  // namespace
+
+// Users per shared-memory tile of the dense pass (a 64 KB tile of b).
+int dense_tile_users(const Params &P) {
+    long long per = (long long)P.M * P.K * 4;
+    long long T = DENSE_TILE_BYTES / per;
+    if (T > 256) T = 256;
+    if (T >= 4) T &= ~3LL;
+    if (T < 1) T = 1;
+    return (int)T;
+}
+
+size_t dense_smem_bytes(const Params &P, int mode) {
+    return smem_layout(KP_B_DENSE, P.K, P.M, 64, DENSE_THREADS, P.tile ? P.tile : dense_tile_users(P), mode).total;
+}
+
+cudaError_t launch_batch_pass(const BatchDev &B, int maxm, size_t smem, int grid, const double *lam,
+                              int mode, int round, uint32_t *x_all, cudaStream_t st) {
+    return batch_dispatch(B, maxm, smem, grid, lam, mode, round, x_all, st, nullptr);
+}
+
+// Persistent grid of the batched pass: SM count x resident blocks of the histogram mode.
+int batch_grid_size(int maxm, size_t smem) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    BatchDev dummy{};
+    int occ = 0;
+    for (int mode = 0; mode < 3; ++mode) {
+        int o = 0;
+        if (batch_dispatch(dummy, maxm, smem, 1, nullptr, mode, 0, nullptr, 0, &o) != cudaSuccess || o < 1) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        occ = mode == 0 ? o : (o < occ ? o : occ);
+    }
+    if (occ > 4) occ = 4;
+    return sms * occ;
+}
 
 cudaError_t launch_user_pass(const Params &P, const Scratch &S, const double *lambda, int mode,
                              int round, uint32_t *x_bits, cudaStream_t st) {

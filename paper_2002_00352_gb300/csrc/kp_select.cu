@@ -30,9 +30,9 @@ __device__ __forceinline__ unsigned long long budget_fixed(double Bk, int fixs) 
     return (unsigned long long)floor(v);
 }
 
-__global__ void finalize_kernel(Params P, Scratch S, const double *lam, double *R, double *dual,
-                                double *primal, double *g, double alpha, double *lam_next,
-                                int do_dd) {
+__device__ __forceinline__ void finalize_body(const Params &P, const Scratch &S, const double *lam,
+                                              double *R, double *dual, double *primal, double *g,
+                                              double alpha, double *lam_next, int do_dd) {
     const int K = P.K;
     if (threadIdx.x == 0) {
         const double io = ldexp(1.0, -P.fixo);
@@ -60,6 +60,28 @@ __global__ void finalize_kernel(Params P, Scratch S, const double *lam, double *
     }
 }
 
+__global__ void finalize_kernel(Params P, Scratch S, const double *lam, double *R, double *dual,
+                                double *primal, double *g, double alpha, double *lam_next,
+                                int do_dd) {
+    finalize_body(P, S, lam, R, dual, primal, g, alpha, lam_next, do_dd);
+}
+
+// one block per instance of a batch; outputs (if given) at the instance's offsets
+__global__ void batch_finalize_kernel(BatchDev B, const double *lam, double *R, double *dual,
+                                      double *primal, double alpha, double *lam_next, int do_dd) {
+    __shared__ Params sP;
+    __shared__ Scratch sS;
+    const int i = blockIdx.x;
+    if (threadIdx.x == 0) {
+        sP = B.P[i];
+        sS = B.S[i];
+    }
+    __syncthreads();
+    const int64_t ko = B.koff[i];
+    finalize_body(sP, sS, lam + ko, R ? R + ko : nullptr, dual ? dual + i : nullptr,
+                  primal ? primal + i : nullptr, nullptr, alpha, lam_next ? lam_next + ko : nullptr, do_dd);
+}
+
 // exact selection among the buffered breakpoints of knapsack k with key in
 // [lo, hi): the key at which the mass accumulated from the top first exceeds
 // `need`.  Block-wide; returns the key to every thread.
@@ -84,9 +106,9 @@ __device__ uint32_t exact_select(const Scratch &S, const Params &P, int k, uint3
         const int nd = (int)(((width - 1) >> sh) + 1);
         for (int d = threadIdx.x; d < NSUB; d += blockDim.x) h[d] = 0ull;
         __syncthreads();
-        for (int gblk = 0; gblk < S.G; ++gblk) {
-            const uint32_t cnt = S.bufcnt[(size_t)k * S.G + gblk];
-            const uint2 *base = S.buf + ((size_t)k * S.G + gblk) * S.cap_kb;
+        for (int gblk = 0; gblk < S.gspan; ++gblk) {
+            const uint32_t cnt = S.bufcnt[(size_t)k * S.gspan + gblk];
+            const uint2 *base = S.buf + ((size_t)k * S.gspan + gblk) * S.cap_kb;
             for (uint32_t s = threadIdx.x; s < cnt; s += blockDim.x) {
                 const uint2 e = base[s];
                 const uint32_t off = e.x - clo;
@@ -157,8 +179,8 @@ __device__ __forceinline__ void unresolved(Scratch &S, SelK &sk, uint32_t lo, ui
     atomicAdd(&S.ctr->n_unres[round + 1], 1);
 }
 
-__global__ void select_kernel(Params P, Scratch S, const double *lam, double *lam_next, int round) {
-    const int k = blockIdx.x;
+__device__ __forceinline__ void select_body(const Params &P, Scratch &S, int k, const double *lam,
+                                            double *lam_next, int round) {
     __shared__ SelK sk;
     __shared__ unsigned long long row[NSUB];
     __shared__ int s_pick;
@@ -276,6 +298,27 @@ __global__ void select_kernel(Params P, Scratch S, const double *lam, double *la
         }
         S.sel[k] = sk;
     }
+}
+
+__global__ void select_kernel(Params P, Scratch S, const double *lam, double *lam_next, int round) {
+    select_body(P, S, blockIdx.x, lam, lam_next, round);
+}
+
+// one block per (instance, knapsack) of a batch
+__global__ void batch_select_kernel(BatchDev B, const double *lam, double *lam_next, int round) {
+    __shared__ Params sP;
+    __shared__ Scratch sS;
+    __shared__ int s_skip;
+    const int i = B.kinst[blockIdx.x];
+    const int64_t ko = B.koff[i];
+    if (threadIdx.x == 0) {
+        sP = B.P[i];
+        sS = B.S[i];
+        s_skip = round > 0 && sS.ctr->n_unres[round] == 0;
+    }
+    __syncthreads();
+    if (s_skip) return;
+    select_body(sP, sS, (int)(blockIdx.x - ko), lam + ko, lam_next + ko, round);
 }
 
 __global__ void backward_kernel(int64_t N, int M, int W, int K, const double *lam,
@@ -409,6 +452,19 @@ cudaError_t launch_finalize(const Params &P, const Scratch &S, const double *lam
                             double *lambda_next, cudaStream_t st) {
     finalize_kernel<<<1, 256, 0, st>>>(P, S, lambda, R, dual, primal, g, alpha, lambda_next,
                                        lambda_next != nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchDev &B, const double *lam, double *R, double *dual,
+                                  double *primal, double alpha, double *lam_next, cudaStream_t st) {
+    batch_finalize_kernel<<<B.count, 256, 0, st>>>(B, lam, R, dual, primal, alpha, lam_next,
+                                                   lam_next != nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_select(const BatchDev &B, int64_t totK, const double *lam,
+                                double *lam_next, int round, cudaStream_t st) {
+    batch_select_kernel<<<(unsigned)totK, 256, 0, st>>>(B, lam, lam_next, round);
     return cudaGetLastError();
 }
 

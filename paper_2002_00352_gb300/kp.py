@@ -53,7 +53,8 @@ EXPORTS = [
     "kp_create", "kp_destroy", "kp_solve_users", "kp_reduce_consumption", "kp_dual_value",
     "kp_dd_step", "kp_scd_breakpoints", "kp_threshold_select", "kp_scd_step",
     "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_last_error", "kp_version",
-    "kp_reduce_consumption_noalloc",
+    "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
+    "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
 ]
 
 
@@ -77,6 +78,13 @@ def load_library(path: Optional[str] = None):
     lib.kp_device_status.argtypes = [P, P]
     lib.kp_select_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
     lib.kp_reduce_consumption_noalloc.argtypes = [ctypes.POINTER(kp_desc), P, P, P, P, P, P, P]
+    lib.kp_batch_create.argtypes = [ctypes.POINTER(kp_desc), i32, ctypes.POINTER(ctypes.c_void_p)]
+    lib.kp_batch_destroy.argtypes = [P]
+    lib.kp_batch_layout.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.kp_batch_reduce_consumption.argtypes = [P, P, P, P, P, P, P]
+    lib.kp_batch_dd_step.argtypes = [P, P, f64, P, P]
+    lib.kp_batch_scd_step.argtypes = [P, P, P, P]
+    lib.kp_batch_device_status.argtypes = [P, P]
     lib.kp_last_error.restype = ctypes.c_char_p
     lib.kp_version.restype = ctypes.c_int
     for name in EXPORTS:
@@ -288,3 +296,66 @@ def unpack_x(x_bits: torch.Tensor, N: int, M: int) -> torch.Tensor:
     w = x_bits.view(N, W).to(torch.int64) & 0xFFFFFFFF
     j = torch.arange(M, device=x_bits.device)
     return ((w[:, j // 32] >> (j % 32)) & 1).to(torch.uint8)
+
+
+class Batch:
+    """A kp_batch handle: many dense instances solved by shared launches."""
+
+    def __init__(self, handle, insts, koff):
+        self.handle = handle
+        self.insts = insts
+        self.koff = koff                    # python list, len count + 1
+        self.count = len(insts)
+        self.totK = koff[-1]
+        self.xoff = [0]
+        for inst in insts:
+            self.xoff.append(self.xoff[-1] + inst.N * ((inst.M + 31) // 32))
+
+    def close(self):
+        if self.handle:
+            load_library().kp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kp_batch_create(insts) -> Batch:
+    """kp_batch_create over a list of dense gen.Instance on the GPU."""
+    lib = load_library()
+    arr = (kp_desc * len(insts))()
+    keep = []
+    for q, inst in enumerate(insts):
+        d, k = _desc(inst.N, inst.M, inst.K, inst.p, inst.B, inst.S, inst.C, inst.b, None, None, None, None)
+        arr[q] = d
+        keep.append(k)
+    h = ctypes.c_void_p()
+    _check(lib.kp_batch_create(arr, len(insts), ctypes.byref(h)))
+    koff = (ctypes.c_int64 * (len(insts) + 1))()
+    _check(lib.kp_batch_layout(h, koff))
+    return Batch(h, list(insts), list(koff))
+
+
+def kp_batch_reduce_consumption(batch: Batch, lam, R=None, dual_sum=None, primal_sum=None, x_bits=None,
+                                stream=None):
+    _check(load_library().kp_batch_reduce_consumption(
+        batch.handle, _ptr(lam, torch.float64, "lambda"), _ptr(R, torch.float64, "R"),
+        _ptr(dual_sum, torch.float64, "dual_sum"), _ptr(primal_sum, torch.float64, "primal_sum"),
+        _ptr(x_bits, None, "x_bits"), _stream(stream)))
+
+
+def kp_batch_dd_step(batch: Batch, lam, alpha, lam_next, stream=None):
+    _check(load_library().kp_batch_dd_step(batch.handle, _ptr(lam, torch.float64, "lambda"), float(alpha),
+                                           _ptr(lam_next, torch.float64, "lambda_next"), _stream(stream)))
+
+
+def kp_batch_scd_step(batch: Batch, lam, lam_next, stream=None):
+    _check(load_library().kp_batch_scd_step(batch.handle, _ptr(lam, torch.float64, "lambda"),
+                                            _ptr(lam_next, torch.float64, "lambda_next"), _stream(stream)))
+
+
+def kp_batch_device_status(batch: Batch, stream=None):
+    _check(load_library().kp_batch_device_status(batch.handle, _stream(stream)))

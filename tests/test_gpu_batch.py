@@ -1,0 +1,81 @@
+"""Batched solving of many independent instances (one persistent launch per pass)
+against the per-instance path and the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2002_00352_gb300 import gen, kp
+from tests.gpu_util import compare_state, lam_close
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances(count=9, seed=4, n_hi=20_000):
+    specs = gen.batched_specs(count=count, seed=seed, n_lo=300, n_hi=n_hi, m_lo=2, m_hi=20, k_lo=1, k_hi=12)
+    return [gen.batched_instance(sp, device="cuda") for sp in specs]
+
+
+def test_batch_scd_equals_per_instance():
+    insts = _instances()
+    batch = kp.kp_batch_create(insts)
+    probs = [kp.kp_create_from_instance(x) for x in insts]
+    rng = np.random.default_rng(1)
+    lam = torch.tensor(rng.uniform(0, 0.3, batch.totK), dtype=torch.float64, device="cuda")
+    for step in range(4):
+        nxt = torch.zeros_like(lam)
+        kp.kp_batch_scd_step(batch, lam, nxt)
+        kp.kp_batch_device_status(batch)
+        for i, (x, pr) in enumerate(zip(insts, probs)):
+            a, b = batch.koff[i], batch.koff[i + 1]
+            one = torch.zeros(x.K, dtype=torch.float64, device="cuda")
+            kp.kp_scd_step(pr, lam[a:b].contiguous(), one)
+            assert torch.equal(one, nxt[a:b]), (step, i)
+        lam = nxt
+
+
+def test_batch_scd_matches_oracle_one_step():
+    insts = _instances(count=5, seed=8, n_hi=3000)
+    batch = kp.kp_batch_create(insts)
+    rng = np.random.default_rng(2)
+    lam_h = rng.uniform(0, 0.4, batch.totK)
+    lam = torch.tensor(lam_h, device="cuda")
+    nxt = torch.zeros_like(lam)
+    kp.kp_batch_scd_step(batch, lam, nxt)
+    kp.kp_batch_device_status(batch)
+    got = nxt.cpu().numpy()
+    for i, x in enumerate(insts):
+        a, b = batch.koff[i], batch.koff[i + 1]
+        p, bb = x.to_dense_numpy()
+        want, _, _ = oracle.scd_step(p, bb, x.S, x.C, lam_h[a:b], x.B.cpu().numpy())
+        assert np.all(lam_close(got[a:b], want)), (i, got[a:b], want)
+
+
+def test_batch_consumption_and_dd():
+    insts = _instances(count=7, seed=9, n_hi=5000)
+    batch = kp.kp_batch_create(insts)
+    rng = np.random.default_rng(3)
+    lam_h = rng.uniform(0, 0.5, batch.totK)
+    lam = torch.tensor(lam_h, device="cuda")
+    R = torch.zeros(batch.totK, dtype=torch.float64, device="cuda")
+    d = torch.zeros(batch.count, dtype=torch.float64, device="cuda")
+    pr = torch.zeros(batch.count, dtype=torch.float64, device="cuda")
+    x = torch.zeros(batch.xoff[-1], dtype=torch.int32, device="cuda")
+    kp.kp_batch_reduce_consumption(batch, lam, R=R, dual_sum=d, primal_sum=pr, x_bits=x)
+    nxt = torch.zeros_like(lam)
+    kp.kp_batch_dd_step(batch, lam, 1e-3, nxt)
+    torch.cuda.synchronize()
+    for i, inst in enumerate(insts):
+        a, b = batch.koff[i], batch.koff[i + 1]
+        p, bb = inst.to_dense_numpy()
+        xo, Ro, do, po = oracle.user_pass(p, bb, inst.S, inst.C, lam_h[a:b])
+        xs = kp.unpack_x(x[batch.xoff[i]:batch.xoff[i + 1]], inst.N, inst.M).cpu().numpy().astype(np.int32)
+        compare_state(p, bb, lam_h[a:b], xs, R[a:b].cpu().numpy(), float(d[i]), float(pr[i]), xo, Ro, do, po)
+        want = oracle.dd_update(lam_h[a:b], R[a:b].cpu().numpy(), inst.B.cpu().numpy(), 1e-3)
+        assert np.allclose(nxt[a:b].cpu().numpy(), want, rtol=1e-12, atol=1e-15)
+
+
+def test_batch_rejects_csr():
+    x = gen.random_small(100, 4, 3, seed=1, device="cuda", layout="csr")
+    with pytest.raises(Exception):
+        kp.kp_batch_create([x])
