@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--ref-sample", type=int, default=4000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-nhi", type=int, default=1_000_000)
     return ap.parse_args()
 
 
@@ -215,8 +217,68 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_batched(args):
+    """256 independent dense instances (N log-uniform in [1e3, 1e6], M in 5..50, K in 1..64,
+    total cap C in 1..M/2): SCD steps of the whole batch by the batched path, and the
+    same steps by looping the per-instance path over the instances."""
+    import torch
+    from paper_2002_00352_gb300 import gen, kp
+    torch.cuda.set_device(0)
+    specs = gen.batched_specs(count=args.batch_count, n_hi=args.batch_nhi)
+    insts = [gen.batched_instance(sp, device="cuda") for sp in specs]
+    batch = kp.kp_batch_create(insts)
+    probs = [kp.kp_create_from_instance(x) for x in insts]
+    totK = batch.totK
+    koff = batch.koff
+
+    def batched_steps(n, lam):
+        nxt = torch.empty_like(lam)
+        for _ in range(n):
+            kp.kp_batch_scd_step(batch, lam, nxt)
+            lam, nxt = nxt, lam
+        return lam
+
+    def looped_steps(n, lam):
+        nxt = torch.empty_like(lam)
+        for _ in range(n):
+            for i, pr in enumerate(probs):
+                kp.kp_scd_step(pr, lam[koff[i]:koff[i + 1]], nxt[koff[i]:koff[i + 1]])
+            lam, nxt = nxt, lam
+        return lam
+
+    res = {}
+    for name, fn in (("batched", batched_steps), ("looped", looped_steps)):
+        lam = torch.zeros(totK, dtype=torch.float64, device="cuda")
+        lam = fn(args.warmup, lam)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lam = fn(args.steps, lam)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = (e0.elapsed_time(e1), lam.cpu())
+    kp.kp_batch_device_status(batch)
+    same = bool(torch.equal(res["batched"][1], res["looped"][1]))
+    ms_b, ms_l = res["batched"][0], res["looped"][0]
+    n = len(insts)
+    users = sum(x.N for x in insts)
+    out = {"metric": "batched SCD instances*iters/s (256 instances)", "value": n * args.steps / (ms_b / 1e3),
+           "unit": "instances*iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{n} dense instances, N log-uniform [1e3, {args.batch_nhi:.0e}], M 5..50, "
+                                  f"K 1..64, total cap 1..M/2", "users": users, "total_knapsacks": totK,
+                      "instance_bytes": sum(x.nbytes() for x in insts),
+                      "looped_value": n * args.steps / (ms_l / 1e3), "looped_ms_per_step": ms_l / args.steps,
+                      "speedup_vs_looped": ms_l / ms_b, "same_lambda_as_looped": same}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "batched_256":
+        run_batched(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

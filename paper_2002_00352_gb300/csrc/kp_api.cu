@@ -234,10 +234,10 @@ fail_out:
 }
 
 // Allocates the handle's scratch for blocks [g_lo, g_lo + gspan) of a grid of G
-// blocks; budget = breakpoint-buffer entries; ctr = counters owned elsewhere
-// (a batch pools them) or nullptr to allocate.
+// blocks; budget = breakpoint-buffer entries; ctr, bufcnt = counters and
+// buffer counts owned elsewhere (a batch pools them) or nullptr to allocate.
 kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget,
-                        kp::Counters *ctr) {
+                        kp::Counters *ctr, uint32_t *bufcnt) {
     kp_status st = KP_OK;
     const kp::Params &P = h->P;
     {
@@ -254,7 +254,10 @@ kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget
         if ((st = alloc(h, &S.reg3, K * 3, "window masses")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.subhist, K * kp::NSUB, "sub-histogram")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.buf, K * GS * (size_t)S.cap_kb, "breakpoint buffer")) != KP_OK) goto fail_out;
-        if ((st = alloc(h, &S.bufcnt, K * GS, "buffer counts")) != KP_OK) goto fail_out;
+        if (bufcnt)
+            S.bufcnt = bufcnt;
+        else if ((st = alloc(h, &S.bufcnt, K * GS, "buffer counts")) != KP_OK)
+            goto fail_out;
         if ((st = alloc(h, &S.ovf, K, "overflow flags")) != KP_OK) goto fail_out;
         if ((st = alloc(h, &S.sel, K, "selection state")) != KP_OK) goto fail_out;
         if (ctr)

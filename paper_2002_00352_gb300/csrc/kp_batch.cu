@@ -20,6 +20,9 @@ struct kp_batch {
     int64_t totK = 0, ntiles = 0;
     kp::BatchDev B{};
     kp::Counters *ctr = nullptr;
+    uint32_t *bufcnt = nullptr;
+    size_t bufcnt_words = 0;
+    unsigned long long *next = nullptr;
     std::vector<void *> allocs;
     std::vector<int64_t> koff;
 };
@@ -96,30 +99,72 @@ kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out) {
         destroy(b);
         return bfail(KP_ECUDA, "kp_batch_create: no resident block fits the shared memory of the batch");
     }
-    // work list: tiles of every instance, in instance order
+    // estimated work of one user: the kinetic sweep per knapsack grows like M^3
+    // (M lines, O(M^2) swaps, O(M) scan each); plus the reduced costs (M K)
+    auto user_cost = [](const kp::Params &P) {
+        const double m = (double)P.M;
+        return (double)P.K * (m * m * (m + 8.0) / 8.0 + m + 16.0);
+    };
+    double total = 0.0;
+    for (int i = 0; i < count; ++i) total += user_cost(b->probs[i]->P) * (double)b->probs[i]->P.N;
+    // tiles of at most a quarter of a block's share of the work
+    const double tile_target = total / (4.0 * b->G);
+    for (int i = 0; i < count; ++i) {
+        kp::Params &P = b->probs[i]->P;
+        const double t = std::floor(tile_target / user_cost(P));
+        if (t < (double)P.tile) P.tile = t < 1.0 ? 1 : (int)t;
+    }
+    for (int m = 0; m < 3; ++m) {
+        b->smem[m] = 0;
+        for (int i = 0; i < count; ++i) b->smem[m] = std::max(b->smem[m], kp::dense_smem_bytes(b->probs[i]->P, m));
+    }
+    // work list: the tiles of every instance, most expensive instances first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return user_cost(b->probs[a]->P) > user_cost(b->probs[c]->P);
+    });
     std::vector<int32_t> tile_inst;
     std::vector<int64_t> tile_u0, xoff(count);
-    std::vector<int64_t> tstart(count), tend(count);
     b->koff.assign(count + 1, 0);
     int64_t xo = 0;
     for (int i = 0; i < count; ++i) {
         const kp::Params &P = b->probs[i]->P;
-        tstart[i] = (int64_t)tile_inst.size();
-        for (int64_t u0 = 0; u0 < P.N; u0 += P.tile) {
-            tile_inst.push_back(i);
-            tile_u0.push_back(u0);
-        }
-        tend[i] = (int64_t)tile_inst.size();
         b->koff[i + 1] = b->koff[i] + P.K;
         xoff[i] = xo;
         xo += P.N * P.W;
     }
+    for (int i : order) {
+        const kp::Params &P = b->probs[i]->P;
+        for (int64_t u0 = 0; u0 < P.N; u0 += P.tile) {
+            tile_inst.push_back(i);
+            tile_u0.push_back(u0);
+        }
+    }
     b->ntiles = (int64_t)tile_inst.size();
     b->totK = b->koff[count];
-    const int64_t per = (b->ntiles + b->G - 1) / b->G;
     std::vector<int32_t> kinst(b->totK);
     for (int i = 0; i < count; ++i)
         for (int64_t k = b->koff[i]; k < b->koff[i + 1]; ++k) kinst[k] = i;
+    {  // buffer counts of every instance in one array, cleared before each pass
+        void *p = nullptr;
+        b->bufcnt_words = (size_t)b->totK * b->G;
+        cudaError_t e = cudaMalloc(&p, sizeof(uint32_t) * b->bufcnt_words);
+        if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof(uint32_t) * b->bufcnt_words);
+        if (e != cudaSuccess) {
+            destroy(b);
+            return bfail(KP_ENOMEM, "batch buffer counts", e);
+        }
+        b->allocs.push_back(p);
+        b->bufcnt = static_cast<uint32_t *>(p);
+        e = cudaMalloc(&p, sizeof(unsigned long long) * (kp::MAX_REFINE + 1));
+        if (e != cudaSuccess) {
+            destroy(b);
+            return bfail(KP_ENOMEM, "batch tile counters", e);
+        }
+        b->allocs.push_back(p);
+        b->next = static_cast<unsigned long long *>(p);
+    }
     {
         void *p = nullptr;
         cudaError_t e = cudaMalloc(&p, sizeof(kp::Counters) * count);
@@ -135,10 +180,10 @@ kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out) {
     std::vector<kp::Scratch> hS(count);
     for (int i = 0; i < count && st == KP_OK; ++i) {
         kp_problem *h = b->probs[i];
-        const int g_lo = (int)(tstart[i] / per), g_hi = (int)((tend[i] - 1) / per);
         double budget = 4.0 * (double)h->P.N * h->P.M;
         budget = std::min(std::max(budget, (double)(1 << 16)), (double)(1 << 24));
-        st = kp_impl::alloc_scratch(h, b->G, g_lo, g_hi - g_lo + 1, budget, b->ctr + i);
+        st = kp_impl::alloc_scratch(h, b->G, 0, b->G, budget, b->ctr + i,
+                                    b->bufcnt + (size_t)b->koff[i] * b->G);
         hP[i] = h->P;
         hS[i] = h->S;
     }
@@ -155,6 +200,7 @@ kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out) {
     }
     b->B.ntiles = b->ntiles;
     b->B.count = count;
+    b->B.next = b->next;
     *out = b;
     return KP_OK;
 }
@@ -172,11 +218,21 @@ kp_status kp_batch_layout(kp_batch *b, int64_t *koff) {
     return KP_OK;
 }
 
+// Clears the tile counters of a step and, for passes that buffer breakpoints,
+// the buffer counts of every (instance, knapsack, block).
+static cudaError_t reset_pass(kp_batch *b, bool counters, bool counts, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (counters) e = cudaMemsetAsync(b->next, 0, sizeof(unsigned long long) * (kp::MAX_REFINE + 1), st);
+    if (e == cudaSuccess && counts) e = cudaMemsetAsync(b->bufcnt, 0, sizeof(uint32_t) * b->bufcnt_words, st);
+    return e;
+}
+
 kp_status kp_batch_reduce_consumption(kp_batch *b, const double *lambda, double *R, double *dual_sum,
                                       double *primal_sum, uint32_t *x_bits, void *stream) {
     if (!b || !lambda) return bfail(KP_EINVAL, "kp_batch_reduce_consumption: NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_STATE], b->G, lambda,
+    cudaError_t e = reset_pass(b, true, false, st);
+    if (e == cudaSuccess) e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_STATE], b->G, lambda,
                                           kp::MODE_STATE, 0, x_bits, st);
     if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, R, dual_sum, primal_sum, 0.0, nullptr, st);
     if (e != cudaSuccess) return bfail(KP_ECUDA, "batch consumption pass", e);
@@ -188,8 +244,10 @@ kp_status kp_batch_dd_step(kp_batch *b, const double *lambda, double alpha, doub
     if (!b || !lambda || !lambda_next) return bfail(KP_EINVAL, "kp_batch_dd_step: NULL argument");
     if (!(alpha >= 0.0)) return bfail(KP_EINVAL, "kp_batch_dd_step: alpha must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_STATE], b->G, lambda,
-                                          kp::MODE_STATE, 0, nullptr, st);
+    cudaError_t e = reset_pass(b, true, false, st);
+    if (e == cudaSuccess)
+        e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_STATE], b->G, lambda, kp::MODE_STATE, 0,
+                                  nullptr, st);
     if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, nullptr, nullptr, nullptr, alpha, lambda_next, st);
     if (e != cudaSuccess) return bfail(KP_ECUDA, "batch dual-descent step", e);
     return KP_OK;
@@ -202,13 +260,16 @@ kp_status kp_batch_scd_step(kp_batch *b, const double *lambda, double *lambda_ne
     // clear every instance's counters except its status word
     cudaError_t e = cudaMemset2DAsync(b->ctr, sizeof(kp::Counters), 0, offsetof(kp::Counters, status),
                                       (size_t)b->count, st);
+    if (e == cudaSuccess) e = reset_pass(b, true, true, st);
     if (e == cudaSuccess)
         e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_HIST], b->G, lambda, kp::MODE_HIST, 0,
                                   nullptr, st);
     if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, nullptr, nullptr, nullptr, 0.0, nullptr, st);
     if (e == cudaSuccess) e = kp::launch_batch_select(b->B, b->totK, lambda, lambda_next, 0, st);
     for (int r = 1; r <= kp::MAX_REFINE && e == cudaSuccess; ++r) {
-        e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_REFINE], b->G, lambda, kp::MODE_REFINE, r,
+        e = reset_pass(b, false, true, st);
+        if (e == cudaSuccess)
+            e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_REFINE], b->G, lambda, kp::MODE_REFINE, r,
                                   nullptr, st);
         if (e == cudaSuccess) e = kp::launch_batch_select(b->B, b->totK, lambda, lambda_next, r, st);
     }

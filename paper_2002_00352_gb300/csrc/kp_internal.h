@@ -95,8 +95,9 @@ struct Scratch {
 
 enum PassMode { MODE_STATE = 0, MODE_HIST = 1, MODE_REFINE = 2 };
 
-// Many independent instances processed by one persistent launch: the tile
-// list is ordered by instance; block b takes tiles [b * per, (b + 1) * per).
+// Many independent instances processed by one persistent launch: blocks take
+// tiles from a shared counter; the tile list holds the most expensive
+// instances first, each instance's tiles consecutive.
 struct BatchDev {
     const Params *P;        // [count]
     Scratch *S;             // [count]
@@ -105,6 +106,7 @@ struct BatchDev {
     const int32_t *kinst;   // [sum K] instance of every global knapsack index
     const int32_t *tile_inst;  // [ntiles]
     const int64_t *tile_u0;    // [ntiles]
+    unsigned long long *next;  // [MAX_REFINE + 1] tile counters, one per pass of a step
     int64_t ntiles;
     int32_t count;
 };
@@ -153,5 +155,6 @@ struct kp_problem {
 namespace kp_impl {
 // kp_api.cu: validation + parameters, and scratch for blocks [g_lo, g_lo + gspan)
 kp_status prepare(const kp_desc *d, kp_problem *h);
-kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget, kp::Counters *ctr);
+kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget, kp::Counters *ctr,
+                        uint32_t *bufcnt = nullptr);
 }  // namespace kp_impl

@@ -931,10 +931,11 @@ __global__ void __launch_bounds__(THREADS) dense_pass_kernel(Params P, Scratch S
 }
 
 // Batched pass: one persistent launch over the tiles of many dense instances.
-// The tile list is ordered by instance and every block takes a contiguous
-// range of it, so a block switches instance rarely; at a switch it flushes the
-// previous instance's block state into that instance's scratch and loads the
-// next instance's parameters and multipliers.
+// Blocks take tiles from the pass's counter; consecutive tiles belong to the
+// same instance, so a block switches instance rarely; at a switch it flushes
+// the previous instance's block state into that instance's scratch and loads
+// the next instance's parameters and multipliers.  Every sum is an integer
+// sum, so the result does not depend on which block took which tile.
 template <int MAXM, int MODE, int THREADS>
 __global__ void __launch_bounds__(THREADS) dense_batch_kernel(BatchDev B, const double *lam_all,
                                                               uint32_t *x_all, int round) {
@@ -942,13 +943,15 @@ __global__ void __launch_bounds__(THREADS) dense_batch_kernel(BatchDev B, const 
     __shared__ Params sP;
     __shared__ Scratch sS;
     __shared__ int s_skip;
-    const int64_t per = (B.ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = t0 + per < B.ntiles ? t0 + per : B.ntiles;
+    __shared__ long long s_t;
     int cur = -1;
     unsigned long long dsum = 0ull, psum = 0ull;
     SmemLayout L;
-    for (int64_t t = t0; t < t1; ++t) {
+    for (;;) {
+        if (threadIdx.x == 0) s_t = (long long)atomicAdd(&B.next[round], 1ull);
+        __syncthreads();
+        const int64_t t = s_t;
+        if (t >= B.ntiles) break;
         const int inst = B.tile_inst[t];
         if (inst != cur) {
             if (cur >= 0 && !s_skip) flush_block_state<MODE>(sP, sS, L, smem, dsum, psum);
@@ -962,7 +965,7 @@ __global__ void __launch_bounds__(THREADS) dense_batch_kernel(BatchDev B, const 
             cur = inst;
             dsum = psum = 0ull;
             L = smem_layout(KP_B_DENSE, sP.K, sP.M, MAXM, THREADS, sP.tile, MODE);
-            if (!s_skip) init_block_state<MODE>(sP, sS, lam_all + B.koff[inst], L, smem, round, t == 0 || B.tile_inst[t - 1] != inst);
+            if (!s_skip) init_block_state<MODE>(sP, sS, lam_all + B.koff[inst], L, smem, round, B.tile_u0[t] == 0);
             __syncthreads();
         }
         if (s_skip) continue;
