@@ -226,6 +226,14 @@ kp_status kp_reduce_consumption_noalloc(const kp_desc *desc, const double *lambd
                                         double *dual_sum, double *primal_sum, double *g,
                                         uint32_t *x_bits, void *stream);
 
+/* Autotuner: times the breakpoint pass of a dense instance on its first
+ * min(N, 2^18) users at several tile sizes (users staged per shared-memory
+ * tile: the default, 8, 16, 32, 64, 128, 256 where they fit) and keeps the
+ * fastest for every later call on the handle; *chosen (may be NULL) receives
+ * it.  A CSR instance has no run-time tile size (*chosen = 0).  Synchronous;
+ * allocates K doubles for the duration of the call.  (Not in the paper.) */
+kp_status kp_autotune(kp_problem *h, int32_t *chosen, void *stream);
+
 /* Synchronises the stream and returns the device-side status accumulated by
  * the handle's kernels since the last call (KP_OK, KP_ETIMEOUT or
  * KP_ESTATE), then clears it. */

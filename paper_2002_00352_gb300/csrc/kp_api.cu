@@ -408,6 +408,63 @@ kp_status kp_dual_backward(kp_problem *h, const double *lambda, const uint32_t *
     return KP_OK;
 }
 
+kp_status kp_autotune(kp_problem *h, int32_t *chosen, void *stream) {
+    if (!check_handle(h)) return fail(KP_EINVAL, "kp_autotune: NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    kp::Params &P = h->P;
+    if (P.layout != KP_B_DENSE) {  // the CSR pass has no run-time tile parameter
+        if (chosen) *chosen = 0;
+        return KP_OK;
+    }
+    // time the breakpoint pass on a prefix of the users at every candidate tile size
+    kp::Params Q = P;
+    Q.N = P.N < (1 << 18) ? P.N : (1 << 18);
+    double *lam = nullptr;
+    KP_CUDA(cudaMalloc(&lam, sizeof(double) * P.K), "cudaMalloc");
+    KP_CUDA(cudaMemsetAsync(lam, 0, sizeof(double) * P.K, st), "cudaMemsetAsync");
+    cudaEvent_t e0, e1;
+    KP_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+    KP_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+    const int def = kp::dense_tile_users(P);
+    int best = def;
+    float best_ms = -1.f;
+    const int cands[] = {def, 8, 16, 32, 64, 128, 256};
+    for (int c : cands) {
+        if (c > def && c != def) continue;  // larger tiles than the default do not fit its shared memory budget
+        Q.tile = c;
+        cudaError_t e = kp::launch_user_pass(Q, h->S, lam, kp::MODE_HIST, 0, nullptr, st);  // warm
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+            e = kp::launch_user_pass(Q, h->S, lam, kp::MODE_HIST, 0, nullptr, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(lam);
+    // the timed passes accumulated into the scratch: clear what the next call consumes
+    kp::Scratch &S = h->S;
+    KP_CUDA(cudaMemsetAsync(S.Rfix, 0, sizeof(unsigned long long) * P.K, st), "cudaMemsetAsync");
+    KP_CUDA(cudaMemsetAsync(S.objfix, 0, sizeof(unsigned long long) * 2, st), "cudaMemsetAsync");
+    KP_CUDA(cudaMemsetAsync(S.reg3, 0, sizeof(unsigned long long) * 3 * P.K, st), "cudaMemsetAsync");
+    KP_CUDA(cudaMemsetAsync(S.ovf, 0, sizeof(uint32_t) * P.K, st), "cudaMemsetAsync");
+    KP_CUDA(cudaMemsetAsync(S.ctr, 0, sizeof(kp::Counters), st), "cudaMemsetAsync");
+    KP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    P.tile = best;
+    if (chosen) *chosen = best;
+    return KP_OK;
+}
+
 kp_status kp_device_status(kp_problem *h, void *stream) {
     if (!check_handle(h)) return fail(KP_EINVAL, "kp_device_status: NULL handle");
     cudaStream_t st = (cudaStream_t)stream;

@@ -1023,7 +1023,7 @@ cudaError_t launch_csr(const Params &P, const Scratch &S, const double *lam, uin
 template <int MAXM, int MODE>
 cudaError_t launch_dense(const Params &P, const Scratch &S, const double *lam, uint32_t *x_bits,
                          int round, cudaStream_t st, int *occupancy_out) {
-    int T = dense_tile_users(P);
+    const int T = P.tile > 0 ? P.tile : dense_tile_users(P);
     SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, DENSE_THREADS, T, MODE);
     auto kern = dense_pass_kernel<MAXM, MODE, DENSE_THREADS>;
     static int max_dyn = -1;

@@ -55,6 +55,7 @@ EXPORTS = [
     "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_last_error", "kp_version",
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
+    "kp_autotune",
 ]
 
 
@@ -85,6 +86,7 @@ def load_library(path: Optional[str] = None):
     lib.kp_batch_dd_step.argtypes = [P, P, f64, P, P]
     lib.kp_batch_scd_step.argtypes = [P, P, P, P]
     lib.kp_batch_device_status.argtypes = [P, P]
+    lib.kp_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int32), P]
     lib.kp_last_error.restype = ctypes.c_char_p
     lib.kp_version.restype = ctypes.c_int
     for name in EXPORTS:
@@ -284,6 +286,13 @@ def kp_select_stats(prob: Problem, stream=None):
     out = (ctypes.c_int64 * 3)()
     _check(load_library().kp_select_stats(prob.handle, out, _stream(stream)))
     return list(out)
+
+
+def kp_autotune(prob: Problem, stream=None) -> int:
+    """Tile-size autotuner of the dense pass; returns the chosen users per tile."""
+    out = ctypes.c_int32(0)
+    _check(load_library().kp_autotune(prob.handle, ctypes.byref(out), _stream(stream)))
+    return int(out.value)
 
 
 def kp_version() -> int:

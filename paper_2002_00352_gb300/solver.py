@@ -66,19 +66,35 @@ class ScdGraph:
         self.a = lam0.clone()
         self.b = torch.empty_like(self.a)
         self.stats = stats
-        # warm up outside capture (first launches set kernel attributes)
-        s = torch.cuda.Stream()
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            tmp = self.a.clone()
-            tmp2 = torch.empty_like(tmp)
-            scd_step(prob, tmp, tmp2, stats)
-        torch.cuda.current_stream().wait_stream(s)
+        # kernel attributes were set when the handle was created, so capture
+        # needs no warm-up launch (which would also advance the selection state)
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
             scd_step(prob, self.a, self.b, stats)
             scd_step(prob, self.b, self.a, stats)
+
+    def replay(self):
+        self.graph.replay()
+
+    @property
+    def lam(self):
+        return self.a
+
+
+class BatchScdGraph:
+    """Two batched SCD iterations (every instance of a kp.Batch) captured in one CUDA
+    graph; replay() advances all instances by two iterations with one launch."""
+
+    def __init__(self, batch, lam0: torch.Tensor):
+        self.batch = batch
+        self.a = lam0.clone()
+        self.b = torch.empty_like(self.a)
+        torch.cuda.synchronize()  # kernel attributes were set when the batch was created
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            kp.kp_batch_scd_step(batch, self.a, self.b)
+            kp.kp_batch_scd_step(batch, self.b, self.a)
 
     def replay(self):
         self.graph.replay()

@@ -79,3 +79,20 @@ def test_batch_rejects_csr():
     x = gen.random_small(100, 4, 3, seed=1, device="cuda", layout="csr")
     with pytest.raises(Exception):
         kp.kp_batch_create([x])
+
+
+def test_batch_graph_replay_equals_eager():
+    from paper_2002_00352_gb300.solver import BatchScdGraph
+    insts = _instances(count=6, seed=21, n_hi=4000)
+    batch = kp.kp_batch_create(insts)
+    lam0 = torch.zeros(batch.totK, dtype=torch.float64, device="cuda")
+    a = lam0.clone()
+    b = torch.empty_like(a)
+    for _ in range(4):
+        kp.kp_batch_scd_step(batch, a, b)
+        a, b = b, a
+    g = BatchScdGraph(batch, lam0)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(g.lam, a)

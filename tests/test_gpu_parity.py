@@ -297,3 +297,17 @@ def test_graph_replay_matches_eager():
         g.replay()
     torch.cuda.synchronize()
     assert torch.equal(g.lam, eager)
+
+
+def test_autotune_keeps_results():
+    inst = gen.hier_m20(N=30_000, device="cuda")
+    prob = _problem(inst)
+    lam = torch.full((inst.K,), 0.05, dtype=torch.float64, device="cuda")
+    ref = torch.zeros_like(lam)
+    kp.kp_scd_step(prob, lam, ref)
+    tile = kp.kp_autotune(prob)
+    assert tile >= 1
+    got = torch.zeros_like(lam)
+    kp.kp_scd_step(prob, lam, got)
+    kp.kp_device_status(prob)
+    assert torch.equal(got, ref)
