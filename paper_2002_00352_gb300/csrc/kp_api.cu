@@ -190,6 +190,10 @@ kp_status prepare(const kp_desc *d, kp_problem *h) {
         }
         float maxb;
         memcpy(&maxb, &hf[1], 4);
+        if (!(maxb < 0x1p100f)) {  // breakpoints divide by b with the fast reciprocal
+            st = fail(KP_EDATA, "b values must be below 2^100 (max b = %g)", (double)maxb);
+            goto fail_out;
+        }
         double count;
         if (P.layout == KP_B_DENSE) {
             count = (double)P.N * P.M;

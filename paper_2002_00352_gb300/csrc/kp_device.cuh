@@ -300,6 +300,106 @@ __device__ __forceinline__ void sweep_from(const float *pt, int ps, const float 
     }
 }
 
+// Map of Algorithm 4 for one (user, k) in exchange form, for at most JMAX
+// moving lines (slots q < nj: item it[q], slope sl[q] = b_jk > 0).
+//   pt[j*ps]  p~_j at lambda^t;  S  the selection among the fixed lines at
+//   lambda_k = +inf (greedy over the positive items without b_jk)
+// Between events the greedy solution S is constant.  As lambda_k falls a
+// moving line m outside S gains weight w_m = A_m - lambda_k s_m and enters S
+// exactly when w_m exceeds the weakest member of its circuit in S: the
+// selected items of the deepest full set on m's path (matroid exchange,
+// Proposition 1's structure), or 0 when no set on its path is full.  Fixed
+// lines never re-enter once replaced and a moving line leaves S only when a
+// moving line with a larger slope overtakes it, so events are few (the loop
+// bound is only a guard).  Each event emits (lambda_k at the event, the
+// increase of the k-consumption).  The events are the kinetic sweep's consumption
+// changes without its swaps of lines that leave S unchanged.  Divisions use
+// the fast reciprocal (about 2 ulp; b_jk < 2^100 is checked at creation).
+template <int JMAX, typename Mask, class Sink>
+__device__ __forceinline__ void exchange_sweep(const float *pt, int ps, Mask S, int nj,
+                                               const int (&it)[JMAX], const float (&sl)[JMAX],
+                                               float lamk, const Tree &t, int k, Sink &sink) {
+    float A[JMAX];
+    Mask Jm = 0;
+#pragma unroll
+    for (int q = 0; q < JMAX; ++q) {
+        A[q] = q < nj ? fmaf(lamk, sl[q], pt[it[q] * ps]) : -1.f;
+        if (q < nj) Jm |= (Mask)1 << it[q];
+    }
+    uint32_t inq = 0u;  // slots whose item is in S
+    float cur = FLT_MAX;
+    const int guard = 8 * nj * nj + 8;
+    for (int iter = 0; iter < guard; ++iter) {
+        uint32_t full = 0u;
+        for (int l = 0; l < t.L; ++l)
+            if (__popcll((unsigned long long)(S & (Mask)t.items[l])) >= (int)t.cap[l]) full |= 1u << l;
+        float be = 0.f, bv2 = 0.f;
+        int bq = -1;
+        uint32_t bout = 0u;
+        Mask brem = 0;
+#pragma unroll
+        for (int q = 0; q < JMAX; ++q) {
+            if (q < nj && !((inq >> q) & 1u) && A[q] > 0.f) {
+                const uint32_t fm = t.ipath[it[q]] & full;
+                float e, v2 = sl[q];
+                Mask rem = 0;
+                uint32_t outq = 0u;
+                if (!fm) {
+                    e = __fdividef(A[q], sl[q]);  // zero crossing, nothing to replace
+                } else {
+                    const Mask Cm = S & (Mask)t.items[__ffs(fm) - 1];
+                    e = -1.f;
+                    Mask CF = Cm & ~Jm;
+                    if (CF) {  // weakest fixed member (ties: the higher index is weaker)
+                        float wmin = FLT_MAX;
+                        int y = 0;
+                        while (CF) {
+                            const int j = __ffsll((long long)CF) - 1;
+                            CF &= CF - 1;
+                            const float w = pt[j * ps];
+                            if (w <= wmin) {
+                                wmin = w;
+                                y = j;
+                            }
+                        }
+                        e = __fdividef(A[q] - wmin, sl[q]);
+                        rem = (Mask)1 << y;
+                    }
+#pragma unroll
+                    for (int r = 0; r < JMAX; ++r) {
+                        if (r != q && ((inq >> r) & 1u) && ((Cm >> it[r]) & 1) && sl[q] > sl[r]) {
+                            const float x = __fdividef(A[q] - A[r], sl[q] - sl[r]);
+                            if (x > e) {
+                                e = x;
+                                rem = (Mask)1 << it[r];
+                                outq = 1u << r;
+                                v2 = sl[q] - sl[r];
+                            }
+                        }
+                    }
+                }
+                if (e > cur) e = cur;
+                if (e > be) {
+                    be = e;
+                    bq = q;
+                    brem = rem;
+                    bout = outq;
+                    bv2 = v2;
+                }
+            }
+        }
+        if (bq < 0) break;
+        Mask add = 0;
+#pragma unroll
+        for (int q = 0; q < JMAX; ++q)
+            if (q == bq) add = (Mask)1 << it[q];
+        S = (S & ~brem) | add;
+        inq = (inq & ~bout) | (1u << bq);
+        cur = be;
+        sink.emit(k, be, bv2);
+    }
+}
+
 // The walk state (counters, full sets) of a given selection.
 __device__ __forceinline__ Walk walk_of(uint64_t sel, const Tree &t) {
     Walk w;

@@ -90,7 +90,8 @@ struct Scratch {
     uint32_t *ovf;                    // [K]
     SelK *sel;                        // [K]
     Counters *ctr;
-    uint32_t *shmask;                 // [N] CSR: entries whose knapsack another item of the user also uses
+    uint2 *shmask;                    // [N] CSR: .x entries whose knapsack another item of the user
+                                      // also uses, .y the first entry of every such knapsack
 };
 
 enum PassMode { MODE_STATE = 0, MODE_HIST = 1, MODE_REFINE = 2 };
@@ -138,7 +139,7 @@ cudaError_t launch_backward(const Params &P, const double *lambda, const uint32_
                             const double *R, const double *upstream, double *grad_lambda,
                             float *grad_p, double *grad_B, cudaStream_t st);
 cudaError_t launch_validate(const Params &P, uint32_t *flags, cudaStream_t st);
-cudaError_t launch_shmask(const Params &P, uint32_t *shmask, cudaStream_t st);
+cudaError_t launch_shmask(const Params &P, uint2 *shmask, cudaStream_t st);
 // kp_api.cu
 void set_last_error(const char *msg);
 

@@ -295,24 +295,14 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
     for (int j = 0; j < M; ++j) mg[j] = pt[j] - mg[j];
     uint32_t pending = 0;  // first entries of the knapsacks shared by several items
     if (nnz <= 32) {
-        const uint32_t shm = S.shmask[i];
+        const uint2 shm = S.shmask[i];
+        pending = shm.y;
         int e = 0;
         for (int j = 0; j < M; ++j) {
             const int c = nzr[j];
             const float m = mg[j];
             for (int q = 0; q < c; ++q, ++e) {
-                if ((shm >> e) & 1u) {
-                    const int k = kid[e];
-                    uint32_t earlier = shm & ((1u << e) - 1u);
-                    bool first = true;
-                    while (earlier) {
-                        const int f = __ffs(earlier) - 1;
-                        earlier &= earlier - 1;
-                        if (kid[f] == k) first = false;
-                    }
-                    if (first) pending |= 1u << e;
-                    continue;
-                }
+                if ((shm.x >> e) & 1u) continue;
                 const float v = __ldg(val + e);
                 if (!(v > 0.f)) continue;
                 const int k = kid[e];
@@ -405,7 +395,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                                                   int64_t e0, const float4 *kinfo,
                                                   unsigned long long *rfix, unsigned long long &dsum,
                                                   unsigned long long &psum, uint32_t *x_bits,
-                                                  Sink &sink, float *prow) {
+                                                  Sink &sink, float *prow, uint32_t &shared_entries) {
     constexpr int EC = C > 0 ? MAXM * C : 1;
     const int M = P.M;
     const Tree &T = P.tree;
@@ -554,11 +544,17 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
         // data-dependent branches: for every full set l, minSel[l] is the
         // weakest selected item of l and maxCut[l] the best rejected item whose
         // deepest full set is l
-        float minSel[KP_MAX_L], maxCut[KP_MAX_L];
+        // ts_j = max over the sets on j's path of their best cut item (j
+        // selected), tn_j = the weakest selected item of j's deepest full set
         const uint32_t rej = pos & ~G;
         int dy[MAXM];
+        float ts[MAXM], tn[MAXM];
 #pragma unroll
-        for (int y = 0; y < MAXM; ++y) dy[y] = __ffs(T.ipath[y] & full) - 1;
+        for (int y = 0; y < MAXM; ++y) {
+            dy[y] = __ffs(T.ipath[y] & full) - 1;
+            ts[y] = 0.f;
+            tn[y] = 0.f;
+        }
         for (int l = 0; l < T.L; ++l) {
             const uint32_t selL = G & (uint32_t)T.items[l];
             float mn = FLT_MAX, mx = 0.f;
@@ -567,27 +563,21 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 mn = ((selL >> j) & 1u) ? fminf(mn, pt[j]) : mn;
                 mx = (((rej >> j) & 1u) && dy[j] == l) ? fmaxf(mx, pt[j]) : mx;
             }
-            minSel[l] = mn;
-            maxCut[l] = mx;
+#pragma unroll
+            for (int j = 0; j < MAXM; ++j) {
+                ts[j] = ((T.ipath[j] >> l) & 1u) ? fmaxf(ts[j], mx) : ts[j];
+                tn[j] = dy[j] == l ? mn : tn[j];
+            }
         }
         float *mrow = prow + (size_t)blockDim.x * MAXM;  // this thread's margin row
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-            float ts = 0.f;
-            uint32_t path = T.ipath[j];
-            while (path) {  // the same path in every lane
-                const int l = __ffs(path) - 1;
-                path &= path - 1;
-                ts = fmaxf(ts, maxCut[l]);
-            }
-            const float tn = dy[j] >= 0 ? minSel[dy[j] < 0 ? 0 : dy[j]] : 0.f;
-            mrow[j] = pt[j] - (((G >> j) & 1u) ? ts : tn);
-        }
+        for (int j = 0; j < MAXM; ++j) mrow[j] = pt[j] - (((G >> j) & 1u) ? ts[j] : tn[j]);
         // Algorithm 4 Map: closed form for knapsacks only one item touches.  One
         // rolled copy of the emission body keeps the code in the instruction
         // cache; entries are re-read from L1.
-        const uint32_t shm = S.shmask[i];
-        uint32_t pending = 0u;
+        const uint2 shm = S.shmask[i];
+        const uint32_t pending = shm.y;
+        shared_entries = shm.x;
         int e = 0;
 #pragma unroll 1
         for (int j = 0; j < M; ++j) {
@@ -595,18 +585,8 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
             const int c = C > 0 ? C : (int)nzr[j];
 #pragma unroll 1
             for (int q = 0; q < c; ++q, ++e) {
+                if ((shm.x >> e) & 1u) continue;
                 const int k = kid[e];
-                if ((shm >> e) & 1u) {
-                    uint32_t earlier = shm & ((1u << e) - 1u);
-                    bool firstk = true;
-                    while (earlier) {
-                        const int f = __ffs(earlier) - 1;
-                        earlier &= earlier - 1;
-                        if ((int)kid[f] == k) firstk = false;
-                    }
-                    if (firstk) pending |= 1u << e;
-                    continue;
-                }
                 const float v = __ldg(val + e);
                 if (v > 0.f) {
                     const float4 ki = kinfo[k];
@@ -626,34 +606,59 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
     }
 }
 
-// One shared-knapsack sweep: the owner's p~ row is in shared memory, its
-// entries are read again to collect the slopes b_jk of knapsack k.
+// One shared-knapsack sweep: the owner's p~ row and rank masks are in shared
+// memory; the slopes b_jk of knapsack k are collected from the owner's shared
+// entries (shm).  Up to XMAX moving lines run the exchange form of the sweep
+// with every per-line value in registers; more fall back to the kinetic sweep.
+constexpr int XMAX = 3;
+
 template <int MAXM, int C, class Sink>
-__device__ __noinline__ void sweep_task(const Params &P, const float4 *kinfo, const float *prow,
-                                        const uint32_t *brow, int64_t i, int64_t e0, int e, Sink &sink) {
+__device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo, const float *prow,
+                                           const uint32_t *brow, int64_t i, int64_t e0, uint32_t shm,
+                                           int e, Sink &sink) {
     const int M = P.M;
     const Tree &T = P.tree;
     const uint8_t *nzr = P.innz + (size_t)i * M;
     const float *val = P.val + e0;
     const int16_t *kid = P.kidx + e0;
     const int k = kid[e];
-    float sv[MAXM];
-    uint32_t J = 0, pos = 0;
-    int f = 0;
-    for (int j2 = 0; j2 < M; ++j2) {
-        const int c2 = C > 0 ? C : (int)nzr[j2];
-        sv[j2] = 0.f;
-        if (prow[j2] > 0.f) pos |= 1u << j2;
-        for (int q2 = 0; q2 < c2; ++q2, ++f)
-            if (kid[f] == k) {
-                const float vv = __ldg(val + f);
-                if (vv > 0.f) {
-                    sv[j2] = vv;
-                    J |= 1u << j2;
-                }
-            }
+    int it[XMAX];
+    float sl[XMAX];
+#pragma unroll
+    for (int q = 0; q < XMAX; ++q) {
+        it[q] = 0;
+        sl[q] = 0.f;
     }
-    // selection among the fixed lines: Algorithm 1 over pos \ J with the
+    int nj = 0;
+    uint32_t J = 0;
+    uint32_t r = shm;
+    while (r) {  // entries of knapsack k are among the shared entries
+        const int f = __ffs(r) - 1;
+        r &= r - 1;
+        if (kid[f] != k) continue;
+        int j2;
+        if constexpr (C > 0) {
+            j2 = f / C;
+        } else {
+            int acc = 0;
+            j2 = 0;
+            while (acc + (int)nzr[j2] <= f) acc += nzr[j2++];
+        }
+        const float vv = __ldg(val + f);
+#pragma unroll
+        for (int q = 0; q < XMAX; ++q)
+            if (q == nj) {
+                it[q] = j2;
+                sl[q] = vv;
+            }
+        ++nj;
+        J |= 1u << j2;
+    }
+    uint32_t pos = 0;
+#pragma unroll
+    for (int j2 = 0; j2 < MAXM; ++j2)
+        if (j2 < M && prow[j2] > 0.f) pos |= 1u << j2;
+    // selection among the fixed lines: Algorithm 1 over pos \\ J with the
     // owner's rank masks
     uint32_t SF = pos & ~J;
     for (int l = 0; l < T.L; ++l) {
@@ -665,7 +670,23 @@ __device__ __noinline__ void sweep_task(const Params &P, const float4 *kinfo, co
             if (((inl >> j) & 1u) && __popc(brow[j] & inl) >= cap) drop |= 1u << j;
         SF &= ~drop;
     }
-    sweep_from<MAXM>(prow, 1, sv, 1, M, J, kinfo[k].x, T, k, walk_of(SF, T), sink);
+    if (nj <= XMAX) {
+        exchange_sweep<XMAX, uint32_t>(prow, 1, SF, nj, it, sl, kinfo[k].x, T, k, sink);
+        return;
+    }
+    float sv[MAXM];
+#pragma unroll
+    for (int j2 = 0; j2 < MAXM; ++j2) sv[j2] = 0.f;
+    int f = 0;
+    for (int j2 = 0; j2 < M; ++j2) {
+        const int c2 = C > 0 ? C : (int)nzr[j2];
+        for (int q2 = 0; q2 < c2; ++q2, ++f)
+            if (kid[f] == k) {
+                const float vv = __ldg(val + f);
+                if (vv > 0.f) sv[j2] = vv;
+            }
+    }
+    sweep_from<MAXM>(prow, 1, sv, 1, M, (uint64_t)J, kinfo[k].x, T, k, walk_of(SF, T), sink);
 }
 
 // The sweeps of a warp's users are pooled and dealt round-robin to its lanes,
@@ -673,10 +694,12 @@ __device__ __noinline__ void sweep_task(const Params &P, const float4 *kinfo, co
 // Called by every lane of the warp.
 template <int MAXM, int C, int THREADS, class Sink>
 __device__ __forceinline__ void warp_sweeps(const Params &P, const float4 *kinfo, float *rows,
-                                            int64_t i, int64_t e0, uint32_t pending, Sink &sink) {
+                                            int64_t i, int64_t e0, uint32_t shm, uint32_t pending,
+                                            Sink &sink) {
     constexpr int QCAP = 64;
     __shared__ uint32_t q[THREADS / 32][QCAP];
     __shared__ long long wi[THREADS], we0[THREADS];
+    __shared__ uint32_t wsh[THREADS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wbase = threadIdx.x & ~31;
     const uint32_t *brows = reinterpret_cast<const uint32_t *>(rows + 2 * (size_t)THREADS * MAXM);
     const int n = __popc(pending);
@@ -691,32 +714,27 @@ __device__ __forceinline__ void warp_sweeps(const Params &P, const float4 *kinfo
     if (pending) {
         wi[threadIdx.x] = i;
         we0[threadIdx.x] = e0;
+        wsh[threadIdx.x] = shm;
     }
-    int slot = x - n;
-    uint32_t pm = pending;
-    while (pm) {
-        const int e = __ffs(pm) - 1;
-        pm &= pm - 1;
-        if (slot < QCAP) q[warp][slot] = ((uint32_t)lane << 5) | (uint32_t)e;
-        ++slot;
+    for (int done = 0; done < total; done += QCAP) {  // the same trip count in every lane
+        int slot = x - n;
+        uint32_t pm = pending;
+        while (pm) {
+            const int e = __ffs(pm) - 1;
+            pm &= pm - 1;
+            if (slot >= done && slot < done + QCAP) q[warp][slot - done] = ((uint32_t)lane << 5) | (uint32_t)e;
+            ++slot;
+        }
+        __syncwarp();
+        const int nq = total - done < QCAP ? total - done : QCAP;
+        for (int t = lane; t < nq; t += 32) {
+            const uint32_t d = q[warp][t];
+            const int owner = wbase + (int)(d >> 5);
+            sweep_task<MAXM, C>(P, kinfo, rows + (size_t)owner * MAXM, brows + (size_t)owner * MAXM,
+                                wi[owner], we0[owner], wsh[owner], (int)(d & 31u), sink);
+        }
+        __syncwarp();
     }
-    __syncwarp();
-    const int nq = total < QCAP ? total : QCAP;
-    for (int t = lane; t < nq; t += 32) {
-        const uint32_t d = q[warp][t];
-        const int owner = wbase + (int)(d >> 5);
-        sweep_task<MAXM, C>(P, kinfo, rows + (size_t)owner * MAXM, brows + (size_t)owner * MAXM, wi[owner], we0[owner], (int)(d & 31u), sink);
-    }
-    // tasks beyond the queue's capacity stay with their owners
-    slot = x - n;
-    pm = pending;
-    while (pm) {
-        const int e = __ffs(pm) - 1;
-        pm &= pm - 1;
-        if (slot >= QCAP) sweep_task<MAXM, C>(P, kinfo, rows + (size_t)threadIdx.x * MAXM, brows + (size_t)threadIdx.x * MAXM, i, e0, e, sink);
-        ++slot;
-    }
-    __syncwarp();
 }
 
 template <int MAXM, int C, int MODE, int THREADS, class Sink>
@@ -748,13 +766,13 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
             const int excl = block_excl_scan<THREADS>(nnz, s_scan);
             e0 = s_base + excl;
         }
-        uint32_t pending = 0u;
+        uint32_t pending = 0u, shm = 0u;
         if (valid) {
             bool done = false;
             if constexpr (MAXM <= 16) {
                 if (nnz <= 32) {
                     pending = csr_user_fast<MAXM, C, MODE>(P, S, i, e0, kinfo, rfix, dsum, psum, x_bits,
-                                                           sink, rows + (size_t)threadIdx.x * MAXM);
+                                                           sink, rows + (size_t)threadIdx.x * MAXM, shm);
                     done = true;
                 }
             }
@@ -764,7 +782,7 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
             }
         }
         if constexpr (MODE != MODE_STATE) {
-            if constexpr (MAXM <= 16) warp_sweeps<MAXM, C, THREADS>(P, kinfo, rows, i, e0, pending, sink);
+            if constexpr (MAXM <= 16) warp_sweeps<MAXM, C, THREADS>(P, kinfo, rows, i, e0, shm, pending, sink);
         }
         if constexpr (C == 0) __syncthreads();
     }

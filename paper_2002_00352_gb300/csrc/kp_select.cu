@@ -412,15 +412,17 @@ int sm_count() {
     return sms;
 }
 
-// For every user with at most 32 entries: bit e set iff entry e has b > 0 and
-// another item of the same user has an entry with the same knapsack and b > 0.
-__global__ void shmask_kernel(Params P, uint32_t *shmask) {
+// For every user with at most 32 entries: bit e of .x set iff entry e has
+// b > 0 and another item of the same user has an entry with the same knapsack
+// and b > 0; bit e of .y set iff entry e is the first such entry of its
+// knapsack.
+__global__ void shmask_kernel(Params P, uint2 *shmask) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
         const int64_t e0 = P.uoff[i];
         const int64_t nnz = P.uoff[i + 1] - e0;
         if (nnz > 32) {
-            shmask[i] = 0u;
+            shmask[i] = make_uint2(0u, 0u);
             continue;
         }
         int owner[32];
@@ -429,20 +431,28 @@ __global__ void shmask_kernel(Params P, uint32_t *shmask) {
             const int c = P.innz[i * P.M + j];
             for (int q = 0; q < c && e < 32; ++q) owner[e++] = j;
         }
-        uint32_t m = 0;
+        uint32_t m = 0, first = 0;
         for (int a = 0; a < (int)nnz; ++a) {
             if (!(P.val[e0 + a] > 0.f)) continue;
             const int ka = P.kidx[e0 + a];
+            bool sh = false, earlier = false;
             for (int b = 0; b < (int)nnz; ++b)
-                if (owner[b] != owner[a] && P.kidx[e0 + b] == ka && P.val[e0 + b] > 0.f) m |= 1u << a;
+                if (b != a && P.kidx[e0 + b] == ka && P.val[e0 + b] > 0.f) {
+                    if (owner[b] != owner[a]) sh = true;
+                    if (b < a) earlier = true;
+                }
+            if (sh) {
+                m |= 1u << a;
+                if (!earlier) first |= 1u << a;
+            }
         }
-        shmask[i] = m;
+        shmask[i] = make_uint2(m, first);
     }
 }
 
 }  // namespace
 
-cudaError_t launch_shmask(const Params &P, uint32_t *shmask, cudaStream_t st) {
+cudaError_t launch_shmask(const Params &P, uint2 *shmask, cudaStream_t st) {
     shmask_kernel<<<sm_count() * 8, 256, 0, st>>>(P, shmask);
     return cudaGetLastError();
 }
