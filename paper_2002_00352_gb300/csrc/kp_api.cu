@@ -217,11 +217,8 @@ kp_status prepare(const kp_desc *d, kp_problem *h) {
             }
         }
         // fixed-point mass: every per-knapsack sum is below count * max b
-        double bound = count * (double)maxb + 1.0;
-        int s = (int)std::floor(62.0 - std::log2(bound));
-        if (s > 40) s = 40;
-        if (s < 4) s = 4;
-        P.fixs = s;
+        P.fixs = kp::mass_shift(count, maxb);
+        P.bscale = std::ldexp(1.0f, P.fixs);
         // objective sums: every per-user value is below M * max p
         float maxp;
         memcpy(&maxp, &hf[2], 4);

@@ -171,6 +171,13 @@ __device__ __forceinline__ uint32_t key_of(float v) {
     return k > 0x7F7FFFFFu ? 0x7F7FFFFFu : k;
 }
 
+// Mass of one entry in units of 2^-fixs: round(v * 2^fixs) (to nearest even),
+// below 2^30 for every b of the instance (Params::bscale = 2^fixs): the
+// scaling is exact and the conversion is a single 32-bit one.
+__device__ __forceinline__ unsigned long long bmass(float v, float bscale) {
+    return (unsigned long long)__float2uint_rn(v * bscale);
+}
+
 // round(v * 2^s) for finite v >= 0, with integer operations only (on GB300
 // the FP64 pipe, which also converts floats to 64-bit integers, is narrow).
 // Halves round up.  s is chosen at creation so that no sum can overflow.
@@ -315,63 +322,69 @@ __device__ __forceinline__ void sweep_from(const float *pt, int ps, const float 
 // increase of the k-consumption).  The events are the kinetic sweep's consumption
 // changes without its swaps of lines that leave S unchanged.  Divisions use
 // the fast reciprocal (about 2 ulp; b_jk < 2^100 is checked at creation).
-template <int JMAX, typename Mask, class Sink>
-__device__ __forceinline__ void exchange_sweep(const float *pt, int ps, Mask S, int nj,
+template <int MAXM>
+__device__ __forceinline__ float pick(const float (&w)[MAXM], int j) {
+    float r = w[0];
+#pragma unroll
+    for (int q = 1; q < MAXM; ++q) r = j == q ? w[q] : r;
+    return r;
+}
+
+// w[j] = p~_j at lambda^t (registers, M <= MAXM <= 32)
+template <int JMAX, int MAXM, class Sink>
+__device__ __forceinline__ void exchange_sweep(const float (&w)[MAXM], uint32_t S, int nj,
                                                const int (&it)[JMAX], const float (&sl)[JMAX],
                                                float lamk, const Tree &t, int k, Sink &sink) {
     float A[JMAX];
-    Mask Jm = 0;
+    uint32_t Jm = 0u, ipq[JMAX];
 #pragma unroll
     for (int q = 0; q < JMAX; ++q) {
-        A[q] = q < nj ? fmaf(lamk, sl[q], pt[it[q] * ps]) : -1.f;
-        if (q < nj) Jm |= (Mask)1 << it[q];
+        A[q] = q < nj ? fmaf(lamk, sl[q], pick(w, it[q])) : -1.f;
+        ipq[q] = q < nj ? t.ipath[it[q]] : 0u;
+        if (q < nj) Jm |= 1u << it[q];
     }
-    uint32_t inq = 0u;  // slots whose item is in S
+    uint32_t inq = 0u, live = 0u;  // slots whose item is in S; slots that can ever enter
+#pragma unroll
+    for (int q = 0; q < JMAX; ++q)
+        if (q < nj && A[q] > 0.f) live |= 1u << q;
     float cur = FLT_MAX;
     const int guard = 8 * nj * nj + 8;
-    for (int iter = 0; iter < guard; ++iter) {
+    for (int iter = 0; iter < guard && (live & ~inq); ++iter) {
         uint32_t full = 0u;
         for (int l = 0; l < t.L; ++l)
-            if (__popcll((unsigned long long)(S & (Mask)t.items[l])) >= (int)t.cap[l]) full |= 1u << l;
+            if (__popc(S & (uint32_t)t.items[l]) >= (int)t.cap[l]) full |= 1u << l;
         float be = 0.f, bv2 = 0.f;
         int bq = -1;
-        uint32_t bout = 0u;
-        Mask brem = 0;
+        uint32_t bout = 0u, brem = 0u;
 #pragma unroll
         for (int q = 0; q < JMAX; ++q) {
-            if (q < nj && !((inq >> q) & 1u) && A[q] > 0.f) {
-                const uint32_t fm = t.ipath[it[q]] & full;
+            if (((live & ~inq) >> q) & 1u) {
+                const uint32_t fm = ipq[q] & full;
                 float e, v2 = sl[q];
-                Mask rem = 0;
-                uint32_t outq = 0u;
+                uint32_t rem = 0u, outq = 0u;
                 if (!fm) {
                     e = __fdividef(A[q], sl[q]);  // zero crossing, nothing to replace
                 } else {
-                    const Mask Cm = S & (Mask)t.items[__ffs(fm) - 1];
-                    e = -1.f;
-                    Mask CF = Cm & ~Jm;
-                    if (CF) {  // weakest fixed member (ties: the higher index is weaker)
-                        float wmin = FLT_MAX;
-                        int y = 0;
-                        while (CF) {
-                            const int j = __ffsll((long long)CF) - 1;
-                            CF &= CF - 1;
-                            const float w = pt[j * ps];
-                            if (w <= wmin) {
-                                wmin = w;
-                                y = j;
-                            }
+                    const uint32_t Cm = S & (uint32_t)t.items[__ffs(fm) - 1];
+                    const uint32_t CF = Cm & ~Jm;
+                    // weakest fixed member (ties: the higher index is weaker)
+                    float wmin = FLT_MAX;
+                    int y = 0;
+#pragma unroll
+                    for (int j = 0; j < MAXM; ++j)
+                        if (((CF >> j) & 1u) && w[j] <= wmin) {
+                            wmin = w[j];
+                            y = j;
                         }
-                        e = __fdividef(A[q] - wmin, sl[q]);
-                        rem = (Mask)1 << y;
-                    }
+                    e = CF ? __fdividef(A[q] - wmin, sl[q]) : -1.f;
+                    rem = CF ? 1u << y : 0u;
 #pragma unroll
                     for (int r = 0; r < JMAX; ++r) {
-                        if (r != q && ((inq >> r) & 1u) && ((Cm >> it[r]) & 1) && sl[q] > sl[r]) {
+                        if (r != q && ((inq >> r) & 1u) && ((Cm >> it[r]) & 1u) && sl[q] > sl[r]) {
                             const float x = __fdividef(A[q] - A[r], sl[q] - sl[r]);
                             if (x > e) {
                                 e = x;
-                                rem = (Mask)1 << it[r];
+                                rem = 1u << it[r];
                                 outq = 1u << r;
                                 v2 = sl[q] - sl[r];
                             }
@@ -389,10 +402,10 @@ __device__ __forceinline__ void exchange_sweep(const float *pt, int ps, Mask S, 
             }
         }
         if (bq < 0) break;
-        Mask add = 0;
+        uint32_t add = 0u;
 #pragma unroll
         for (int q = 0; q < JMAX; ++q)
-            if (q == bq) add = (Mask)1 << it[q];
+            if (q == bq) add = 1u << it[q];
         S = (S & ~brem) | add;
         inq = (inq & ~bout) | (1u << bq);
         cur = be;
@@ -443,6 +456,20 @@ __device__ __forceinline__ uint32_t shared_inc_u32(uint32_t *p) {
     return old;
 }
 
+// red.shared.add.u64 executed only where cond != 0 (predicated, no branch)
+__device__ __forceinline__ void shared_add_u64_if(unsigned long long *p, unsigned long long v, uint32_t cond) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.u64 [%0], %1;\n\t}"
+                 ::"r"(a), "l"(v), "r"(cond) : "memory");
+}
+
+// Breakpoint of a knapsack that one item j of the user touches alone:
+// lambda_k + (p~_j - theta_j) / b_jk, always rounded the same way (no
+// contraction of the addition), so every pass computes identical keys.
+__device__ __forceinline__ float breakpoint_value(float lamk, float margin, float b) {
+    return __fadd_rn(lamk, __fdividef(margin, b));
+}
+
 // ---------------------------------------------------------------------------
 // emission sinks
 // ---------------------------------------------------------------------------
@@ -454,10 +481,11 @@ struct WindowSink {
     uint32_t *bcnt;            // [K] buffer fill of this block (shared)
     uint2 *buf;
     int cap_kb, G, blk;
-    int fixs;
-    __device__ __forceinline__ void emit_ki(int k, const float4 &ki, float v1, float v2) {
+    float bscale;
+    // emission of (v1, v2) whose mass m = bmass(v2, bscale) is already known
+    __device__ __forceinline__ void emit_km(int k, const float4 &ki, float v1, float v2,
+                                            unsigned long long m) {
         if (!(v1 > 0.f)) return;
-        const unsigned long long m = fixmass(v2, fixs);
         const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
         shared_add_u64(&reg3[3 * k + r], m);
         if (r == 1) {
@@ -465,6 +493,19 @@ struct WindowSink {
             if (slot < (uint32_t)cap_kb)
                 buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key_of(v1), __float_as_uint(v2));
         }
+    }
+    __device__ __forceinline__ void emit_ki(int k, const float4 &ki, float v1, float v2) {
+        emit_km(k, ki, v1, v2, bmass(v2, bscale));
+    }
+    // region r of a breakpoint with mass m, where emit holds (predicated)
+    __device__ __forceinline__ void region_add_if(int k, int r, unsigned long long m, bool emit) {
+        shared_add_u64_if(&reg3[3 * k + r], m, emit ? 1u : 0u);
+    }
+    // a breakpoint inside the window whose mass region_add_if took
+    __device__ __forceinline__ void buffer_add(int k, float v1, float v2) {
+        const uint32_t slot = shared_inc_u32(&bcnt[k]);
+        if (slot < (uint32_t)cap_kb)
+            buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key_of(v1), __float_as_uint(v2));
     }
     __device__ __forceinline__ void emit(int k, float v1, float v2) {
         if (!(v2 > 0.f)) return;
@@ -480,23 +521,31 @@ struct RefineSink {
     uint32_t *bcnt;               // [K] (shared)
     uint2 *buf;
     int cap_kb, G, blk;
-    int fixs;
+    float bscale;
     __device__ __forceinline__ void emit(int k, float v1, float v2) {
         if (!(v1 > 0.f) || !(v2 > 0.f)) return;
         const uint32_t key = key_of(v1);
         if (key < lo[k] || key >= hi[k]) return;
         const int sb = (int)((key - lo[k]) >> shift[k]);
-        atomicAdd(&subhist[(size_t)k * NSUB + sb], fixmass(v2, fixs));
+        atomicAdd(&subhist[(size_t)k * NSUB + sb], bmass(v2, bscale));
         const uint32_t slot = shared_inc_u32(&bcnt[k]);
         if (slot < (uint32_t)cap_kb)
             buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key, __float_as_uint(v2));
     }
     __device__ __forceinline__ void emit_ki(int k, const float4 &, float v1, float v2) { emit(k, v1, v2); }
+    __device__ __forceinline__ void emit_km(int k, const float4 &, float v1, float v2, unsigned long long) {
+        emit(k, v1, v2);
+    }
+    __device__ __forceinline__ void region_add_if(int, int, unsigned long long, bool) {}
+    __device__ __forceinline__ void buffer_add(int, float, float) {}
 };
 
 struct NullSink {
     __device__ __forceinline__ void emit(int, float, float) {}
     __device__ __forceinline__ void emit_ki(int, const float4 &, float, float) {}
+    __device__ __forceinline__ void emit_km(int, const float4 &, float, float, unsigned long long) {}
+    __device__ __forceinline__ void region_add_if(int, int, unsigned long long, bool) {}
+    __device__ __forceinline__ void buffer_add(int, float, float) {}
 };
 
 }  // namespace kp

@@ -1,6 +1,7 @@
 // kp_internal.h -- structures shared by the host side of the C ABI and the
 // kernels.  Not part of the public interface (include/kp.h is).
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
@@ -68,6 +69,7 @@ struct Params {
     const int16_t *kidx;
     const double *B;
     int32_t fixs;              // fixed-point shift of b sums: units of 2^-fixs
+    float bscale;              // 2^fixs: the mass of an entry is round(b * bscale) < 2^30
     int32_t fixo;              // fixed-point shift of the objective sums
     int32_t tile;              // dense: users per shared-memory tile
     int32_t creg;              // CSR: every item has exactly creg entries (0: not regular)
@@ -111,6 +113,19 @@ struct BatchDev {
     int64_t ntiles;
     int32_t count;
 };
+
+// Fixed-point unit 2^-s of the b masses: the mass round(b * 2^s) of one entry
+// stays below 2^30 (one 32-bit conversion per entry) and every per-knapsack
+// sum over `count` entries below 2^62.
+inline int mass_shift(double count, float maxb) {
+    const double lb = maxb > 0.f ? std::log2((double)maxb) : -200.0;
+    const int s1 = (int)std::floor(62.0 - std::log2(count * (double)maxb + 1.0));
+    const int s2 = 30 - (int)std::ceil(lb);
+    int s = s1 < s2 ? s1 : s2;
+    if (s > 40) s = 40;
+    if (s < -120) s = -120;
+    return s;
+}
 
 struct PassOut {
     uint32_t *x_bits;  // optional

@@ -165,8 +165,8 @@ kp_status kp_reduce_consumption_noalloc(const kp_desc *d, const double *lambda, 
                     ((P.M * P.creg) % 4 == 0);
         }
     }
-    int fs = (int)std::floor(62.0 - std::log2(count * (double)maxb + 1.0));
-    P.fixs = fs > 40 ? 40 : (fs < 4 ? 4 : fs);
+    P.fixs = kp::mass_shift(count, maxb);
+    P.bscale = std::ldexp(1.0f, P.fixs);
     int fo = (int)std::floor(62.0 - std::log2((double)P.N * P.M * (double)maxp + 1.0));
     P.fixo = fo > 40 ? 40 : (fo < 0 ? 0 : fo);
 

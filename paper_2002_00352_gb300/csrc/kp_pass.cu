@@ -188,7 +188,7 @@ __device__ __forceinline__ WindowSink make_window_sink(const Params &P, const Sc
     ws.cap_kb = S.cap_kb;
     ws.G = S.gspan;
     ws.blk = blockIdx.x - S.g_lo;
-    ws.fixs = P.fixs;
+    ws.bscale = P.bscale;
     return ws;
 }
 
@@ -204,7 +204,7 @@ __device__ __forceinline__ RefineSink make_refine_sink(const Params &P, const Sc
     rs.cap_kb = S.cap_kb;
     rs.G = S.gspan;
     rs.blk = blockIdx.x - S.g_lo;
-    rs.fixs = P.fixs;
+    rs.bscale = P.bscale;
     return rs;
 }
 
@@ -280,7 +280,7 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
                 du += pt[j];
                 pu += __ldg(pr + j);
                 for (int q = 0; q < c; ++q)
-                    shared_add_u64(&rfix[kid[e + q]], fixmass(__ldg(val + e + q), P.fixs));
+                    shared_add_u64(&rfix[kid[e + q]], bmass(__ldg(val + e + q), P.bscale));
             }
             e += c;
         }
@@ -306,7 +306,7 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
                 const float v = __ldg(val + e);
                 if (!(v > 0.f)) continue;
                 const int k = kid[e];
-                sink.emit(k, lamf[k] + __fdividef(m, v), v);
+                sink.emit(k, breakpoint_value(lamf[k], m, v), v);
             }
         }
     } else {
@@ -331,7 +331,7 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
                     f += c2;
                 }
                 if (!shared) {
-                    sink.emit(k, lamf[k] + __fdividef(mg[j], v), v);
+                    sink.emit(k, breakpoint_value(lamf[k], mg[j], v), v);
                 } else if (first) {
                     float s[MAXM];
                     uint64_t J = 0;
@@ -397,6 +397,9 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                                                   unsigned long long &psum, uint32_t *x_bits,
                                                   Sink &sink, float *prow, uint32_t &shared_entries) {
     constexpr int EC = C > 0 ? MAXM * C : 1;
+    // breakpoint pass with every entry in registers: the consumption of the
+    // selected items is taken in the same predicated loop as the breakpoints
+    constexpr bool FOLD = MODE == MODE_HIST && C > 0;
     const int M = P.M;
     const Tree &T = P.tree;
     const float *pr = P.p + (size_t)i * M;
@@ -518,8 +521,9 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 if ((G >> j) & 1u) {
                     du += pt[j];
                     pu += __ldg(pr + j);
+                    if (!FOLD)
 #pragma unroll
-                    for (int q = 0; q < C; ++q) shared_add_u64(&rfix[kk[j * C + q]], fixmass(vv[j * C + q], P.fixs));
+                        for (int q = 0; q < C; ++q) shared_add_u64(&rfix[kk[j * C + q]], bmass(vv[j * C + q], P.bscale));
                 }
         } else {
             int e = 0;
@@ -529,7 +533,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                     du += pt[j];
                     pu += __ldg(pr + j);
                     for (int q = 0; q < cnt[j]; ++q)
-                        shared_add_u64(&rfix[kid[e + q]], fixmass(__ldg(val + e + q), P.fixs));
+                        shared_add_u64(&rfix[kid[e + q]], bmass(__ldg(val + e + q), P.bscale));
                 }
                 e += cnt[j];
             }
@@ -541,11 +545,9 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
         return 0u;
     } else {
         // exchange thresholds theta_j and margins p~_j - theta_j, without
-        // data-dependent branches: for every full set l, minSel[l] is the
-        // weakest selected item of l and maxCut[l] the best rejected item whose
-        // deepest full set is l
-        // ts_j = max over the sets on j's path of their best cut item (j
-        // selected), tn_j = the weakest selected item of j's deepest full set
+        // data-dependent branches: ts_j = max over the sets on j's path of
+        // their best rejected item whose deepest full set it is (j selected),
+        // tn_j = the weakest selected item of j's deepest full set
         const uint32_t rej = pos & ~G;
         int dy[MAXM];
         float ts[MAXM], tn[MAXM];
@@ -570,27 +572,60 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
             }
         }
         float *mrow = prow + (size_t)blockDim.x * MAXM;  // this thread's margin row
+        float mg[MAXM];
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j) mrow[j] = pt[j] - (((G >> j) & 1u) ? ts[j] : tn[j]);
-        // Algorithm 4 Map: closed form for knapsacks only one item touches.  One
-        // rolled copy of the emission body keeps the code in the instruction
-        // cache; entries are re-read from L1.
+        for (int j = 0; j < MAXM; ++j) {
+            mg[j] = pt[j] - (((G >> j) & 1u) ? ts[j] : tn[j]);
+            mrow[j] = mg[j];
+        }
         const uint2 shm = S.shmask[i];
         const uint32_t pending = shm.y;
         shared_entries = shm.x;
-        int e = 0;
-#pragma unroll 1
-        for (int j = 0; j < M; ++j) {
-            const float m = mrow[j];
-            const int c = C > 0 ? C : (int)nzr[j];
-#pragma unroll 1
-            for (int q = 0; q < c; ++q, ++e) {
-                if ((shm.x >> e) & 1u) continue;
+        if constexpr (FOLD) {
+            // Algorithm 4 Map, closed form for knapsacks only one item touches,
+            // and the consumption of the selected items: one predicated pass
+            // over the entries in registers; breakpoints that fall inside the
+            // window are buffered afterwards.
+            uint32_t inside = 0u;
+#pragma unroll
+            for (int e = 0; e < EC; ++e) {
+                const int j = e / C;
+                const float v = vv[e];
+                const int k = kk[e];
+                const float4 ki = kinfo[k];
+                const unsigned long long m = bmass(v, P.bscale);
+                shared_add_u64_if(&rfix[k], m, (G >> j) & 1u);
+                const float v1 = breakpoint_value(ki.x, mg[j], v);
+                const bool emit = v > 0.f && v1 > 0.f && !((shm.x >> e) & 1u);
+                const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
+                sink.region_add_if(k, r, m, emit);
+                inside |= (emit && r == 1) ? 1u << e : 0u;
+            }
+            while (inside) {
+                const int e = __ffs(inside) - 1;
+                inside &= inside - 1;
                 const int k = kid[e];
                 const float v = __ldg(val + e);
-                if (v > 0.f) {
-                    const float4 ki = kinfo[k];
-                    sink.emit_ki(k, ki, ki.x + __fdividef(m, v), v);
+                sink.buffer_add(k, breakpoint_value(kinfo[k].x, mrow[e / C], v), v);
+            }
+        } else {
+            // Algorithm 4 Map: closed form for knapsacks only one item touches.
+            // One rolled copy of the emission body keeps the code in the
+            // instruction cache; entries are re-read from L1.
+            int e = 0;
+#pragma unroll 1
+            for (int j = 0; j < M; ++j) {
+                const float m = mg[j];
+                const int c = C > 0 ? C : (int)nzr[j];
+#pragma unroll 1
+                for (int q = 0; q < c; ++q, ++e) {
+                    if ((shm.x >> e) & 1u) continue;
+                    const int k = kid[e];
+                    const float v = __ldg(val + e);
+                    if (v > 0.f) {
+                        const float4 ki = kinfo[k];
+                        sink.emit_ki(k, ki, breakpoint_value(ki.x, m, v), v);
+                    }
                 }
             }
         }
@@ -654,11 +689,15 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
         ++nj;
         J |= 1u << j2;
     }
-    uint32_t pos = 0;
+    float w[MAXM];
+    uint32_t bt[MAXM], pos = 0;
 #pragma unroll
-    for (int j2 = 0; j2 < MAXM; ++j2)
-        if (j2 < M && prow[j2] > 0.f) pos |= 1u << j2;
-    // selection among the fixed lines: Algorithm 1 over pos \\ J with the
+    for (int j2 = 0; j2 < MAXM; ++j2) {
+        w[j2] = prow[j2];
+        bt[j2] = brow[j2];
+        if (j2 < M && w[j2] > 0.f) pos |= 1u << j2;
+    }
+    // selection among the fixed lines: Algorithm 1 over pos minus J with the
     // owner's rank masks
     uint32_t SF = pos & ~J;
     for (int l = 0; l < T.L; ++l) {
@@ -667,11 +706,11 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
         uint32_t drop = 0u;
 #pragma unroll
         for (int j = 0; j < MAXM; ++j)
-            if (((inl >> j) & 1u) && __popc(brow[j] & inl) >= cap) drop |= 1u << j;
+            if (((inl >> j) & 1u) && __popc(bt[j] & inl) >= cap) drop |= 1u << j;
         SF &= ~drop;
     }
     if (nj <= XMAX) {
-        exchange_sweep<XMAX, uint32_t>(prow, 1, SF, nj, it, sl, kinfo[k].x, T, k, sink);
+        exchange_sweep<XMAX, MAXM>(w, SF, nj, it, sl, kinfo[k].x, T, k, sink);
         return;
     }
     float sv[MAXM];
@@ -909,7 +948,7 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
             while (r) {
                 int j = __ffsll((long long)r) - 1;
                 r &= r - 1;
-                acc += fixmass(bcol[(size_t)j * K], P.fixs);
+                acc += bmass(bcol[(size_t)j * K], P.bscale);
             }
             if (acc) shared_add_u64(&rfix[k], acc);
         }
