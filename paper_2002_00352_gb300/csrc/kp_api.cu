@@ -245,7 +245,39 @@ kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget
         kp::Scratch &S = h->S;
         S.G = G;
         S.g_lo = g_lo;
-        S.gspan = gspan;
+        // CSR: shared-entry masks, and the knapsacks three or more items of one
+        // user use, which a kernel of their own sweeps into extra buffer blocks
+        int rare_grid = 0;
+        if (P.layout == KP_B_CSR) {
+            unsigned long long *cnt = nullptr, n = 0;
+            if ((st = alloc(h, &S.shmask, (size_t)P.N, "shared-entry masks")) != KP_OK) goto fail_out;
+            if ((st = alloc(h, &cnt, 1, "rare-knapsack count")) != KP_OK) goto fail_out;
+            cudaError_t e2 = kp::launch_shmask(P, S.shmask, nullptr, 0, cnt, 0);
+            if (e2 == cudaSuccess) e2 = cudaMemcpy(&n, cnt, sizeof(n), cudaMemcpyDeviceToHost);
+            if (e2 == cudaSuccess && n > 0) {
+                unsigned long long *list = nullptr;
+                if ((st = alloc(h, &list, (size_t)n, "rare-knapsack list")) != KP_OK) goto fail_out;
+                e2 = cudaMemset(cnt, 0, sizeof(unsigned long long));
+                if (e2 == cudaSuccess) e2 = kp::launch_shmask(P, S.shmask, list, (int64_t)n, cnt, 0);
+                S.rare = list;
+                S.nrare = (int64_t)n;
+            }
+            if (e2 == cudaSuccess) e2 = cudaDeviceSynchronize();
+            if (e2 != cudaSuccess) {
+                st = cuda_fail(e2, "shared-entry masks");
+                goto fail_out;
+            }
+            if (S.nrare > 0) {
+                int dev = 0, sms = 1;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                const long long want = (S.nrare + 255) / 256;
+                rare_grid = (int)(want < 2 * sms ? want : 2 * sms);
+            }
+        }
+        S.rare_blk0 = gspan;
+        S.rare_grid = rare_grid;
+        S.gspan = gspan + rare_grid;
         long long cap = (long long)(budget / ((double)P.K * S.gspan));
         if (cap < 64) cap = 64;
         S.cap_kb = (int)cap;
@@ -265,15 +297,6 @@ kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget
             S.ctr = ctr;
         else if ((st = alloc(h, &S.ctr, 1, "counters")) != KP_OK)
             goto fail_out;
-        if (P.layout == KP_B_CSR) {
-            if ((st = alloc(h, &S.shmask, (size_t)P.N, "shared-entry masks")) != KP_OK) goto fail_out;
-            cudaError_t e2 = kp::launch_shmask(P, S.shmask, 0);
-            if (e2 == cudaSuccess) e2 = cudaDeviceSynchronize();
-            if (e2 != cudaSuccess) {
-                st = cuda_fail(e2, "shared-entry masks");
-                goto fail_out;
-            }
-        }
         std::vector<kp::SelK> init(K);
         for (auto &x : init) {
             memset(&x, 0, sizeof(x));

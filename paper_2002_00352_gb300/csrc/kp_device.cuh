@@ -413,6 +413,90 @@ __device__ __forceinline__ void exchange_sweep(const float (&w)[MAXM], uint32_t 
     }
 }
 
+// Sets whose count reached their cap in the selection S.
+__device__ __forceinline__ uint32_t full_sets(uint32_t S, const Tree &t) {
+    uint32_t full = 0u;
+    for (int l = 0; l < t.L; ++l)
+        if (__popc(S & (uint32_t)t.items[l]) >= (int)t.cap[l]) full |= 1u << l;
+    return full;
+}
+
+// Weakest member of the fixed lines CF (ties: the higher index is weaker);
+// ybit = its bit (0 if CF is empty).
+template <int MAXM>
+__device__ __forceinline__ float weakest(const float (&w)[MAXM], uint32_t CF, uint32_t &ybit) {
+    float wmin = FLT_MAX;
+    int y = 0;
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j)
+        if (((CF >> j) & 1u) && w[j] <= wmin) {
+            wmin = w[j];
+            y = j;
+        }
+    ybit = CF ? 1u << y : 0u;
+    return wmin;
+}
+
+// lambda_k at which a moving line (weight A - lambda_k s, path ip) enters the
+// selection S (full sets `full`), whose circuit holds fixed lines and possibly
+// the moving line ob (weight Ao - lambda_k so); rem = the member it replaces.
+// Branch-free: every candidate is computed and the valid one selected.
+template <int MAXM>
+__device__ __forceinline__ float entry_time(const float (&w)[MAXM], const Tree &t, uint32_t S,
+                                            uint32_t full, uint32_t ip, float A, float s, uint32_t ob,
+                                            float Ao, float so, uint32_t &rem) {
+    const uint32_t fm = ip & full;
+    const uint32_t Cm = fm ? S & (uint32_t)t.items[__ffs(fm) - 1] : 0u;
+    uint32_t ybit;
+    const float wmin = weakest(w, Cm & ~ob, ybit);
+    const float ez = __fdividef(A, s);  // zero crossing, nothing to replace
+    const float ec = ybit ? __fdividef(A - wmin, s) : -1.f;
+    const float ex = ((Cm & ob) && s > so) ? __fdividef(A - Ao, s - so) : -1.f;
+    rem = fm ? (ex > ec ? ob : ybit) : 0u;
+    return fm ? fmaxf(ec, ex) : ez;
+}
+
+// exchange_sweep for exactly two moving lines a, b (slot order a, b), as
+// straight-line predicated code: the first line enters, the second enters
+// (possibly overtaking the first), and an overtaken first line re-enters; the
+// line with the larger slope is never overtaken, so there is no fourth event.
+// ki = (lambda_k^t, window) of knapsack k.
+template <int MAXM, class Sink>
+__device__ __forceinline__ void pair_sweep(const float (&w)[MAXM], uint32_t SF, int ia, float sa,
+                                           int ib, float sb, const float4 &ki, const Tree &t, int k,
+                                           Sink &sink) {
+    const float lamk = ki.x;
+    const float Aa = fmaf(lamk, sa, pick(w, ia)), Ab = fmaf(lamk, sb, pick(w, ib));
+    const uint32_t ipa = t.ipath[ia], ipb = t.ipath[ib];
+    uint32_t full = full_sets(SF, t), ra, rb;
+    float ea = entry_time(w, t, SF, full, ipa, Aa, sa, 0u, 0.f, 0.f, ra);
+    float eb = entry_time(w, t, SF, full, ipb, Ab, sb, 0u, 0.f, 0.f, rb);
+    ea = Aa > 0.f ? ea : -1.f;
+    eb = Ab > 0.f ? eb : -1.f;
+    const bool fa = ea >= eb;  // ties: slot a first
+    const float e1 = fa ? ea : eb;
+    const float Af = fa ? Aa : Ab, sf = fa ? sa : sb, Ao = fa ? Ab : Aa, so = fa ? sb : sa;
+    const uint32_t bf = 1u << (fa ? ia : ib), bo = 1u << (fa ? ib : ia);
+    const uint32_t ipf = fa ? ipa : ipb, ipo = fa ? ipb : ipa;
+    const bool ok1 = e1 > 0.f;
+    uint32_t S = (SF & ~(fa ? ra : rb)) | bf;
+    full = full_sets(S, t);
+    uint32_t ro;
+    float e2 = entry_time(w, t, S, full, ipo, Ao, so, bf, Af, sf, ro);
+    e2 = fminf(e2, e1);
+    const bool ok2 = ok1 && Ao > 0.f && e2 > 0.f;
+    const bool over = ok2 && ro == bf;  // the second line overtakes the first
+    S = (S & ~bf) | bo;
+    full = full_sets(S, t);
+    uint32_t r3;
+    float e3 = entry_time(w, t, S, full, ipf, Af, sf, bo, Ao, so, r3);
+    e3 = fminf(e3, e2);
+    const bool ok3 = over && e3 > 0.f;
+    sink.emit_if(k, ki, e1, sf, ok1);
+    sink.emit_if(k, ki, e2, over ? so - sf : so, ok2);
+    sink.emit_if(k, ki, e3, sf, ok3);
+}
+
 // The walk state (counters, full sets) of a given selection.
 __device__ __forceinline__ Walk walk_of(uint64_t sel, const Tree &t) {
     Walk w;
@@ -501,6 +585,14 @@ struct WindowSink {
     __device__ __forceinline__ void region_add_if(int k, int r, unsigned long long m, bool emit) {
         shared_add_u64_if(&reg3[3 * k + r], m, emit ? 1u : 0u);
     }
+    // predicated emission (pred false: nothing); the buffer append is a rare branch
+    __device__ __forceinline__ void emit_if(int k, const float4 &ki, float v1, float v2, bool pred) {
+        const bool go = pred && v1 > 0.f && v2 > 0.f;
+        const unsigned long long m = bmass(v2, bscale);
+        const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
+        shared_add_u64_if(&reg3[3 * k + r], m, go ? 1u : 0u);
+        if (go && r == 1) buffer_add(k, v1, v2);
+    }
     // a breakpoint inside the window whose mass region_add_if took
     __device__ __forceinline__ void buffer_add(int k, float v1, float v2) {
         const uint32_t slot = shared_inc_u32(&bcnt[k]);
@@ -538,6 +630,9 @@ struct RefineSink {
     }
     __device__ __forceinline__ void region_add_if(int, int, unsigned long long, bool) {}
     __device__ __forceinline__ void buffer_add(int, float, float) {}
+    __device__ __forceinline__ void emit_if(int k, const float4 &, float v1, float v2, bool pred) {
+        if (pred) emit(k, v1, v2);
+    }
 };
 
 struct NullSink {
@@ -546,6 +641,7 @@ struct NullSink {
     __device__ __forceinline__ void emit_km(int, const float4 &, float, float, unsigned long long) {}
     __device__ __forceinline__ void region_add_if(int, int, unsigned long long, bool) {}
     __device__ __forceinline__ void buffer_add(int, float, float) {}
+    __device__ __forceinline__ void emit_if(int, const float4 &, float, float, bool) {}
 };
 
 }  // namespace kp

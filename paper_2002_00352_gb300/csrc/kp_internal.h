@@ -93,7 +93,12 @@ struct Scratch {
     SelK *sel;                        // [K]
     Counters *ctr;
     uint2 *shmask;                    // [N] CSR: .x entries whose knapsack another item of the user
-                                      // also uses, .y the first entry of every such knapsack
+                                      // also uses, .y the first entry of every knapsack exactly two
+                                      // items of the user use
+    const unsigned long long *rare;   // [nrare] CSR: (user << 5) | first entry, for the knapsacks
+                                      // that three or more items of one user use
+    int64_t nrare;
+    int32_t rare_blk0, rare_grid;     // buffer blocks [rare_blk0, +rare_grid) of the rare-knapsack kernel
 };
 
 enum PassMode { MODE_STATE = 0, MODE_HIST = 1, MODE_REFINE = 2 };
@@ -154,7 +159,8 @@ cudaError_t launch_backward(const Params &P, const double *lambda, const uint32_
                             const double *R, const double *upstream, double *grad_lambda,
                             float *grad_p, double *grad_B, cudaStream_t st);
 cudaError_t launch_validate(const Params &P, uint32_t *flags, cudaStream_t st);
-cudaError_t launch_shmask(const Params &P, uint2 *shmask, cudaStream_t st);
+cudaError_t launch_shmask(const Params &P, uint2 *shmask, unsigned long long *rare, int64_t cap,
+                          unsigned long long *count, cudaStream_t st);
 // kp_api.cu
 void set_last_error(const char *msg);
 

@@ -147,7 +147,9 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
 template <int MODE>
 __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch &S,
                                                   const SmemLayout &L, unsigned char *smem,
-                                                  unsigned long long dsum, unsigned long long psum) {
+                                                  unsigned long long dsum, unsigned long long psum,
+                                                  int blk = -1) {
+    if (blk < 0) blk = blockIdx.x - S.g_lo;
     const int K = P.K;
     uint32_t *bcnt = (uint32_t *)(smem + L.bcnt);
     unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
@@ -156,7 +158,7 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
         if (MODE != MODE_REFINE && rfix[k]) atomicAdd(&S.Rfix[k], rfix[k]);
         if (MODE != MODE_STATE) {
             uint32_t c = bcnt[k];
-            S.bufcnt[(size_t)k * S.gspan + (blockIdx.x - S.g_lo)] = c < (uint32_t)S.cap_kb ? c : (uint32_t)S.cap_kb;
+            S.bufcnt[(size_t)k * S.gspan + blk] = c < (uint32_t)S.cap_kb ? c : (uint32_t)S.cap_kb;
             if (c > (uint32_t)S.cap_kb) S.ovf[k] = 1u;
         }
     }
@@ -641,12 +643,10 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
     }
 }
 
-// One shared-knapsack sweep: the owner's p~ row and rank masks are in shared
-// memory; the slopes b_jk of knapsack k are collected from the owner's shared
-// entries (shm).  Up to XMAX moving lines run the exchange form of the sweep
-// with every per-line value in registers; more fall back to the kinetic sweep.
-constexpr int XMAX = 3;
-
+// One shared-knapsack sweep (a knapsack exactly two items of the owner use;
+// the others have a kernel of their own, rare_kernel): the owner's p~ row and
+// rank masks are in shared memory, the two slopes b_jk are found among the
+// owner's shared entries (shm).
 template <int MAXM, int C, class Sink>
 __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo, const float *prow,
                                            const uint32_t *brow, int64_t i, int64_t e0, uint32_t shm,
@@ -657,13 +657,8 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
     const float *val = P.val + e0;
     const int16_t *kid = P.kidx + e0;
     const int k = kid[e];
-    int it[XMAX];
-    float sl[XMAX];
-#pragma unroll
-    for (int q = 0; q < XMAX; ++q) {
-        it[q] = 0;
-        sl[q] = 0.f;
-    }
+    int it[2] = {0, 0};
+    float sl[2] = {0.f, 0.f};
     int nj = 0;
     uint32_t J = 0;
     uint32_t r = shm;
@@ -680,12 +675,13 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
             while (acc + (int)nzr[j2] <= f) acc += nzr[j2++];
         }
         const float vv = __ldg(val + f);
-#pragma unroll
-        for (int q = 0; q < XMAX; ++q)
-            if (q == nj) {
-                it[q] = j2;
-                sl[q] = vv;
-            }
+        if (nj == 0) {
+            it[0] = j2;
+            sl[0] = vv;
+        } else {
+            it[1] = j2;
+            sl[1] = vv;
+        }
         ++nj;
         J |= 1u << j2;
     }
@@ -709,23 +705,7 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
             if (((inl >> j) & 1u) && __popc(bt[j] & inl) >= cap) drop |= 1u << j;
         SF &= ~drop;
     }
-    if (nj <= XMAX) {
-        exchange_sweep<XMAX, MAXM>(w, SF, nj, it, sl, kinfo[k].x, T, k, sink);
-        return;
-    }
-    float sv[MAXM];
-#pragma unroll
-    for (int j2 = 0; j2 < MAXM; ++j2) sv[j2] = 0.f;
-    int f = 0;
-    for (int j2 = 0; j2 < M; ++j2) {
-        const int c2 = C > 0 ? C : (int)nzr[j2];
-        for (int q2 = 0; q2 < c2; ++q2, ++f)
-            if (kid[f] == k) {
-                const float vv = __ldg(val + f);
-                if (vv > 0.f) sv[j2] = vv;
-            }
-    }
-    sweep_from<MAXM>(prow, 1, sv, 1, M, (uint64_t)J, kinfo[k].x, T, k, walk_of(SF, T), sink);
+    if (nj == 2) pair_sweep<MAXM>(w, SF, it[0], sl[0], it[1], sl[1], kinfo[k], T, k, sink);
 }
 
 // The sweeps of a warp's users are pooled and dealt round-robin to its lanes,
@@ -820,8 +800,12 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
                 csr_user<MAXM, MODE>(P, S, i, e0, nnz, lamf, ptl, mgl, rfix, dsum, psum, x_bits, sink);
             }
         }
-        if constexpr (MODE != MODE_STATE) {
-            if constexpr (MAXM <= 16) warp_sweeps<MAXM, C, THREADS>(P, kinfo, rows, i, e0, shm, pending, sink);
+        if constexpr (MODE != MODE_STATE && MAXM <= 16) {
+            // all warps of the block sweep at the same time, so the sweep code
+            // and the per-user code do not compete for the instruction cache
+            __syncthreads();
+            warp_sweeps<MAXM, C, THREADS>(P, kinfo, rows, i, e0, shm, pending, sink);
+            __syncthreads();
         }
         if constexpr (C == 0) __syncthreads();
     }
@@ -848,6 +832,132 @@ __global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch 
         csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, ns, dsum, psum);
     }
     flush_block_state<MODE>(P, S, L, smem, dsum, psum);
+}
+
+// Knapsacks that three or more items of one user use (listed at creation; a
+// few per cent of the shared ones): one thread per (user, knapsack), the
+// user's reduced costs recomputed in the same order as the user pass, and
+// Algorithm 4's Map by the exchange form of the sweep (kinetic beyond XMAX
+// moving lines).  Keeping them out of the user pass keeps its sweep phase
+// uniform across the lanes.  The blocks own buffer blocks
+// [rare_blk0, rare_blk0 + rare_grid).
+constexpr int RARE_THREADS = 256;
+constexpr int XMAX = 3;
+
+template <int MAXM, int C, class Sink>
+__device__ __forceinline__ void rare_task(const Params &P, const float4 *kinfo, int64_t i, int e,
+                                          Sink &sink) {
+    const int M = P.M;
+    const Tree &T = P.tree;
+    const int64_t e0 = C > 0 ? P.uoff0 + i * (int64_t)(M * C) : P.uoff[i];
+    const uint8_t *nzr = P.innz + (size_t)i * M;
+    const float *val = P.val + e0;
+    const int16_t *kid = P.kidx + e0;
+    const int k = kid[e];
+    if constexpr (C > 0 && MAXM <= 16) {
+        // registers: reduced costs, rank masks, the moving lines of k
+        float w[MAXM];
+        int it[XMAX] = {0, 0, 0};
+        float sl[XMAX] = {0.f, 0.f, 0.f};
+        int nj = 0;
+        uint32_t J = 0u, pos = 0u;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) {
+            float acc = j < M ? __ldg(P.p + (size_t)i * M + j) : 0.f;
+#pragma unroll
+            for (int q = 0; q < C; ++q) {
+                const int f = j * C + q;
+                const float v = j < M ? __ldg(val + f) : 0.f;
+                const int kk = j < M ? (int)kid[f] : 0;
+                acc = fmaf(-kinfo[kk].x, v, acc);
+                if (j < M && kk == k && v > 0.f) {
+#pragma unroll
+                    for (int s2 = 0; s2 < XMAX; ++s2)
+                        if (s2 == nj) {
+                            it[s2] = j;
+                            sl[s2] = v;
+                        }
+                    ++nj;
+                    J |= 1u << j;
+                }
+            }
+            w[j] = acc;
+            if (j < M && acc > 0.f) pos |= 1u << j;
+        }
+        uint32_t bt[MAXM];
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j) bt[j] = 0u;
+#pragma unroll
+        for (int j = 1; j < MAXM; ++j)
+#pragma unroll
+            for (int j2 = 0; j2 < j; ++j2) {
+                const bool first = w[j2] >= w[j];  // j2 < j wins ties
+                bt[j] |= first ? (1u << j2) : 0u;
+                bt[j2] |= first ? 0u : (1u << j);
+            }
+        uint32_t SF = pos & ~J;  // Algorithm 1 over the fixed lines
+        for (int l = 0; l < T.L; ++l) {
+            const uint32_t inl = SF & (uint32_t)T.items[l];
+            const int cap = T.cap[l];
+            uint32_t drop = 0u;
+#pragma unroll
+            for (int j = 0; j < MAXM; ++j)
+                if (((inl >> j) & 1u) && __popc(bt[j] & inl) >= cap) drop |= 1u << j;
+            SF &= ~drop;
+        }
+        if (nj <= XMAX) {
+            exchange_sweep<XMAX, MAXM>(w, SF, nj, it, sl, kinfo[k].x, T, k, sink);
+            return;
+        }
+    }
+    // general rows, or more than XMAX moving lines: the kinetic sweep
+    float pt[KP_MAX_M], sv[KP_MAX_M];
+    uint64_t Jm = 0;
+    int f = 0;
+    for (int j = 0; j < M; ++j) {
+        float acc = __ldg(P.p + (size_t)i * M + j);
+        sv[j] = 0.f;
+        const int c = C > 0 ? C : (int)nzr[j];
+        for (int q = 0; q < c; ++q, ++f) {
+            const float v = __ldg(val + f);
+            const int kk = kid[f];
+            acc = fmaf(-kinfo[kk].x, v, acc);
+            if (kk == k && v > 0.f) {
+                sv[j] = v;
+                Jm |= 1ull << j;
+            }
+        }
+        pt[j] = acc;
+    }
+    sweep_k<KP_MAX_M>(pt, 1, sv, 1, M, Jm, kinfo[k].x, T, k, sink);
+}
+
+template <int MAXM, int C, int MODE>
+__global__ void __launch_bounds__(RARE_THREADS) rare_kernel(Params P, Scratch S, const double *lam, int round) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
+    const SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, 1, RARE_THREADS, 0, MODE);
+    init_block_state<MODE>(P, S, lam, L, smem, round, false);
+    __syncthreads();
+    const int blk = S.rare_blk0 + blockIdx.x;
+    const float4 *kinfo = (const float4 *)(smem + L.kinfo);
+    auto run = [&](auto &sink) {
+        for (int64_t t = (int64_t)blockIdx.x * RARE_THREADS + threadIdx.x; t < S.nrare;
+             t += (int64_t)gridDim.x * RARE_THREADS) {
+            const unsigned long long rec = S.rare[t];
+            rare_task<MAXM, C>(P, kinfo, (int64_t)(rec >> 5), (int)(rec & 31u), sink);
+        }
+    };
+    if (MODE == MODE_HIST) {
+        WindowSink ws = make_window_sink(P, S, L, smem);
+        ws.blk = blk;
+        run(ws);
+    } else {
+        RefineSink rs = make_refine_sink(P, S, L, smem);
+        rs.blk = blk;
+        run(rs);
+    }
+    flush_block_state<MODE>(P, S, L, smem, 0ull, 0ull, blk);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1194,9 +1304,40 @@ int batch_grid_size(int maxm, size_t smem) {
     return sms * occ;
 }
 
+template <int MAXM, int C, int MODE>
+cudaError_t launch_rare_t(const Params &P, const Scratch &S, const double *lam, int round, cudaStream_t st,
+                          bool prepare_only) {
+    auto kern = rare_kernel<MAXM, C, MODE>;
+    static int max_dyn = -1;  // once per instantiation, before any stream capture
+    cudaError_t e = prepare_kernel(kern, &max_dyn);
+    if (e != cudaSuccess || prepare_only) return e;
+    const SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, 1, RARE_THREADS, 0, MODE);
+    if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
+    kern<<<S.rare_grid, RARE_THREADS, L.total, st>>>(P, S, lam, round);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_rare(const Params &P, const Scratch &S, const double *lam, int round, cudaStream_t st,
+                        bool prepare_only) {
+    if (P.creg == 2 || P.creg == 1) {
+        const bool two = P.creg == 2;
+        if (P.M <= 8) return two ? launch_rare_t<8, 2, MODE>(P, S, lam, round, st, prepare_only)
+                                 : launch_rare_t<8, 1, MODE>(P, S, lam, round, st, prepare_only);
+        if (P.M <= 10) return two ? launch_rare_t<10, 2, MODE>(P, S, lam, round, st, prepare_only)
+                                  : launch_rare_t<10, 1, MODE>(P, S, lam, round, st, prepare_only);
+        if (P.M <= 16) return two ? launch_rare_t<16, 2, MODE>(P, S, lam, round, st, prepare_only)
+                                  : launch_rare_t<16, 1, MODE>(P, S, lam, round, st, prepare_only);
+    }
+    return launch_rare_t<64, 0, MODE>(P, S, lam, round, st, prepare_only);
+}
+
 cudaError_t launch_user_pass(const Params &P, const Scratch &S, const double *lambda, int mode,
                              int round, uint32_t *x_bits, cudaStream_t st) {
-    return dispatch(P, S, lambda, mode, round, x_bits, st, nullptr);
+    cudaError_t e = dispatch(P, S, lambda, mode, round, x_bits, st, nullptr);
+    if (e != cudaSuccess || mode == MODE_STATE || S.nrare == 0 || S.rare_grid == 0) return e;
+    return mode == MODE_HIST ? launch_rare<MODE_HIST>(P, S, lambda, round, st, false)
+                             : launch_rare<MODE_REFINE>(P, S, lambda, round, st, false);
 }
 
 // Persistent grid: SM count x resident blocks of the heaviest mode.
@@ -1215,6 +1356,10 @@ int pass_grid_size(const Params &P) {
     if (dispatch(P, dummy, nullptr, MODE_STATE, 0, nullptr, 0, &occ3) == cudaSuccess && occ3 >= 1 &&
         occ3 < occ)
         occ = occ3;
+    if (P.layout == KP_B_CSR) {  // kernel attributes of the rare-knapsack sweeps
+        launch_rare<MODE_HIST>(P, dummy, nullptr, 0, 0, true);
+        launch_rare<MODE_REFINE>(P, dummy, nullptr, 0, 0, true);
+    }
     (void)cudaGetLastError();  // the queries above report failures through their return values
     if (occ > 4) occ = 4;
     return sms * occ;

@@ -414,9 +414,12 @@ int sm_count() {
 
 // For every user with at most 32 entries: bit e of .x set iff entry e has
 // b > 0 and another item of the same user has an entry with the same knapsack
-// and b > 0; bit e of .y set iff entry e is the first such entry of its
-// knapsack.
-__global__ void shmask_kernel(Params P, uint2 *shmask) {
+// and b > 0; bit e of .y set iff entry e is the first entry of a knapsack that
+// exactly two items of the user use.  Knapsacks used by three or more items
+// are counted in *count and, if rare != nullptr, listed as (user << 5) | first
+// entry (at most cap of them).
+__global__ void shmask_kernel(Params P, uint2 *shmask, unsigned long long *rare, int64_t cap,
+                              unsigned long long *count) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.N; i += stride) {
         const int64_t e0 = P.uoff[i];
@@ -435,15 +438,23 @@ __global__ void shmask_kernel(Params P, uint2 *shmask) {
         for (int a = 0; a < (int)nnz; ++a) {
             if (!(P.val[e0 + a] > 0.f)) continue;
             const int ka = P.kidx[e0 + a];
-            bool sh = false, earlier = false;
+            int users = 1;  // entries of knapsack ka with b > 0 (one per item)
+            bool earlier = false;
             for (int b = 0; b < (int)nnz; ++b)
                 if (b != a && P.kidx[e0 + b] == ka && P.val[e0 + b] > 0.f) {
-                    if (owner[b] != owner[a]) sh = true;
+                    if (owner[b] != owner[a]) ++users;
                     if (b < a) earlier = true;
                 }
-            if (sh) {
+            if (users >= 2) {
                 m |= 1u << a;
-                if (!earlier) first |= 1u << a;
+                if (!earlier) {
+                    if (users == 2) {
+                        first |= 1u << a;
+                    } else {
+                        const unsigned long long slot = atomicAdd(count, 1ull);
+                        if (rare && (int64_t)slot < cap) rare[slot] = ((unsigned long long)i << 5) | (unsigned)a;
+                    }
+                }
             }
         }
         shmask[i] = make_uint2(m, first);
@@ -452,8 +463,9 @@ __global__ void shmask_kernel(Params P, uint2 *shmask) {
 
 }  // namespace
 
-cudaError_t launch_shmask(const Params &P, uint2 *shmask, cudaStream_t st) {
-    shmask_kernel<<<sm_count() * 8, 256, 0, st>>>(P, shmask);
+cudaError_t launch_shmask(const Params &P, uint2 *shmask, unsigned long long *rare, int64_t cap,
+                          unsigned long long *count, cudaStream_t st) {
+    shmask_kernel<<<sm_count() * 8, 256, 0, st>>>(P, shmask, rare, cap, count);
     return cudaGetLastError();
 }
 
