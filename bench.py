@@ -249,8 +249,9 @@ def run_batched(args):
     def graph_steps(n, lam):
         from paper_2002_00352_gb300.solver import BatchScdGraph
         g = graph_cache.get("g")
-        if g is None:
-            g = graph_cache["g"] = BatchScdGraph(batch, lam)
+        if g is None:  # a batch of its own: its selection state starts fresh like the others'
+            graph_cache["batch"] = kp.kp_batch_create(insts)
+            g = graph_cache["g"] = BatchScdGraph(graph_cache["batch"], lam)
         else:
             g.a.copy_(lam)
         for _ in range(n // 2):
@@ -399,7 +400,9 @@ def main():
                          "parallelism": "replicas" if world > 1 else "single GPU",
                          "lambda0": 0.0},
               "roofline": roofline, "clocks": clocks,
-              "gpu_launches": args.steps * (3 + 2 * 4 + 1)}
+              # per step: pass + finalize + select, 4 x (select + re-run pass), backward;
+              # and the rare-knapsack kernel after each of the 5 passes when the instance has some
+              "gpu_launches": args.steps * (3 + 2 * 4 + 1 + (5 if kp.kp_info(prob)["rare_blocks"] > 0 else 0))}
     try:
         st1 = kp.kp_select_stats(prob)
         result["config"]["select_passes_last_step"] = st1[0]

@@ -245,6 +245,13 @@ kp_status kp_device_status(kp_problem *h, void *stream);
  * from the histogram alone (lambda = 0), out[2] = buffer overflows. */
 kp_status kp_select_stats(kp_problem *h, int64_t out[3], void *stream);
 
+/* Launch layout of a handle (host values, no device work): out[0] = blocks of
+ * the user pass, out[1] = users whose knapsacks shared by three or more of
+ * their items are swept by a separate kernel (CSR; each breakpoint pass then
+ * launches one more kernel), out[2] = blocks of that kernel (0 if none),
+ * out[3] = breakpoint-buffer entries per (knapsack, block). */
+kp_status kp_info(kp_problem *h, int64_t out[4]);
+
 /* Thread-local description of the last error on this thread. */
 const char *kp_last_error(void);
 

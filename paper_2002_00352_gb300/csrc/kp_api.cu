@@ -501,6 +501,15 @@ kp_status kp_device_status(kp_problem *h, void *stream) {
     return KP_OK;
 }
 
+kp_status kp_info(kp_problem *h, int64_t out[4]) {
+    if (!check_handle(h) || !out) return fail(KP_EINVAL, "kp_info: NULL argument");
+    out[0] = h->S.G;
+    out[1] = h->S.nrare;
+    out[2] = h->S.rare_grid;
+    out[3] = h->S.cap_kb;
+    return KP_OK;
+}
+
 kp_status kp_select_stats(kp_problem *h, int64_t out[3], void *stream) {
     if (!check_handle(h) || !out) return fail(KP_EINVAL, "kp_select_stats: NULL argument");
     KP_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");

@@ -261,6 +261,28 @@ def random_small(N, M, K, seed, device="cpu", layout="dense", L_groups=None, tot
                     recipe="test instance (csr)")
 
 
+def regular_csr(N, M, K, C, seed, device="cpu", frac=0.1) -> Instance:
+    """CSR with exactly C distinct knapsacks per item (uniform, ascending), values
+    U[0,1], p ~ lognormal(0,1), B = frac * sum b, no local constraints (callers set
+    S, C).  With small K many knapsacks are shared by two or more items of a user."""
+    assert 1 <= C <= K
+    g = _gen(device, seed)
+    p = torch.empty(N * M, dtype=torch.float32, device=device)
+    p.log_normal_(0.0, 1.0, generator=g)
+    keys = torch.rand((N * M, K), generator=g, device=device)
+    ks, _ = torch.sort(torch.argsort(keys, dim=1)[:, :C], dim=1)
+    kidx = ks.reshape(-1).to(torch.int16)
+    val = torch.empty(N * M * C, dtype=torch.float32, device=device).uniform_(0.0, 1.0, generator=g)
+    B = torch.zeros(K, dtype=torch.float64, device=device)
+    B.index_add_(0, kidx.long(), val.double())
+    B = torch.clamp(B * frac, min=1e-3)
+    item_nnz = torch.full((N * M,), C, dtype=torch.uint8, device=device)
+    user_off = torch.arange(N + 1, dtype=torch.int64, device=device) * (M * C)
+    return Instance(name=f"regular_csr_{N}_{M}_{K}_{C}", N=N, M=M, K=K, layout="csr", p=p, B=B,
+                    S=[], C=[], user_off=user_off, item_nnz=item_nnz, val=val, kidx=kidx,
+                    seed=seed, recipe="test instance (regular csr)")
+
+
 WORKLOADS = {
     "dense_N1e4_M10_K5": small_dd_scd,
     "dense_N1e6_M20_K20": hier_m20,

@@ -52,7 +52,7 @@ class kp_desc(ctypes.Structure):
 EXPORTS = [
     "kp_create", "kp_destroy", "kp_solve_users", "kp_reduce_consumption", "kp_dual_value",
     "kp_dd_step", "kp_scd_breakpoints", "kp_threshold_select", "kp_scd_step",
-    "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_last_error", "kp_version",
+    "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_info", "kp_last_error", "kp_version",
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
     "kp_autotune",
@@ -78,6 +78,7 @@ def load_library(path: Optional[str] = None):
     lib.kp_dual_backward.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.kp_device_status.argtypes = [P, P]
     lib.kp_select_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
+    lib.kp_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.kp_reduce_consumption_noalloc.argtypes = [ctypes.POINTER(kp_desc), P, P, P, P, P, P, P]
     lib.kp_batch_create.argtypes = [ctypes.POINTER(kp_desc), i32, ctypes.POINTER(ctypes.c_void_p)]
     lib.kp_batch_destroy.argtypes = [P]
@@ -286,6 +287,13 @@ def kp_select_stats(prob: Problem, stream=None):
     out = (ctypes.c_int64 * 3)()
     _check(load_library().kp_select_stats(prob.handle, out, _stream(stream)))
     return list(out)
+
+
+def kp_info(prob: Problem) -> dict:
+    """Launch layout of a handle (see include/kp.h)."""
+    out = (ctypes.c_int64 * 4)()
+    _check(load_library().kp_info(prob.handle, out))
+    return {"pass_blocks": out[0], "rare_users": out[1], "rare_blocks": out[2], "buffer_per_block": out[3]}
 
 
 def kp_autotune(prob: Problem, stream=None) -> int:

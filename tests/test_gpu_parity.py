@@ -106,6 +106,31 @@ def test_scd_step_parity_random(layout, seed):
         assert np.all(lam_close(got, want)), (got, want)
 
 
+@pytest.mark.parametrize("M,Cn,K,seed", [(10, 2, 6, 21), (8, 2, 5, 22), (16, 2, 9, 23),
+                                         (10, 1, 3, 24), (8, 1, 4, 25), (16, 1, 5, 26)])
+def test_regular_csr_shared_knapsacks(M, Cn, K, seed):
+    """Every item has exactly C entries and K is small, so most knapsacks of a user are
+    used by two of its items (the pair sweep) or by three or more (their own kernel,
+    up to all M items); random laminar families leave more fixed lines selected than
+    the pair sweep keeps in order.  Decisions, consumption and one SCD step against
+    the oracle."""
+    rng = np.random.default_rng(seed)
+    S, C = random_laminar(M, rng, max_nodes=6)
+    inst = gen.regular_csr(3000, M, K, Cn, seed=seed, device="cuda", frac=0.15)
+    inst.S, inst.C = S, C
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    B = inst.B.cpu().numpy()
+    for trial in range(3):
+        lam = rng.uniform(0, 0.8, size=K) * (rng.random(K) < 0.85)
+        x, R, d, pr, g, _ = cuda_state(prob, torch.tensor(lam, device="cuda"))
+        xo, Ro, do, po = oracle.user_pass(p, b, S, C, lam)
+        compare_state(p, b, lam, x, R, d, pr, xo, Ro, do, po)
+        got = _scd_gpu(prob, lam)
+        want, _, _ = oracle.scd_step(p, b, S, C, lam, B)
+        assert np.all(lam_close(got, want)), (trial, got, want)
+
+
 def test_scd_trajectory_small_config():
     """N=1e4, M=10, K=5: 50 SCD iterations; each GPU step matches the oracle's step
     taken at the GPU's own lambda^t."""
