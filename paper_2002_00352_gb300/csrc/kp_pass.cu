@@ -708,18 +708,24 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
     if (nj == 2) pair_sweep<MAXM>(w, SF, it[0], sl[0], it[1], sl[1], kinfo[k], T, k, sink);
 }
 
-// The sweeps of a warp's users are pooled and dealt round-robin to its lanes,
-// so that a user with several shared knapsacks does not keep 31 lanes idle.
-// Called by every lane of the warp.
+// The sweeps of a block's users are pooled and dealt to its threads (about
+// 0.8 per thread on the sparse workload), so that the block, which waits for
+// its slowest warp, takes one round.  All threads of the block sweep at the
+// same time, so the sweep code and the per-user code do not compete for the
+// instruction cache.  Called by every thread of the block; contains the block
+// barriers that make the owners' rows visible and protect them until done.
 template <int MAXM, int C, int THREADS, class Sink>
-__device__ __forceinline__ void warp_sweeps(const Params &P, const float4 *kinfo, float *rows,
-                                            int64_t i, int64_t e0, uint32_t shm, uint32_t pending,
-                                            Sink &sink) {
-    constexpr int QCAP = 64;
-    __shared__ uint32_t q[THREADS / 32][QCAP];
+__device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinfo, float *rows,
+                                             int64_t i, int64_t e0, uint32_t shm, uint32_t pending,
+                                             Sink &sink) {
+    constexpr int QCAP = 2 * THREADS;
+    constexpr int NW = THREADS / 32;
+    static_assert(THREADS <= 2048, "task records hold the owner in 11 bits");
+    __shared__ uint16_t q[QCAP];
     __shared__ long long wi[THREADS], we0[THREADS];
     __shared__ uint32_t wsh[THREADS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wbase = threadIdx.x & ~31;
+    __shared__ int wtot[NW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t *brows = reinterpret_cast<const uint32_t *>(rows + 2 * (size_t)THREADS * MAXM);
     const int n = __popc(pending);
     int x = n;
@@ -728,31 +734,39 @@ __device__ __forceinline__ void warp_sweeps(const Params &P, const float4 *kinfo
         const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    const int total = __shfl_sync(0xffffffffu, x, 31);
-    if (total == 0) return;
+    if (lane == 31) wtot[warp] = x;
     if (pending) {
         wi[threadIdx.x] = i;
         we0[threadIdx.x] = e0;
         wsh[threadIdx.x] = shm;
     }
-    for (int done = 0; done < total; done += QCAP) {  // the same trip count in every lane
-        int slot = x - n;
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < NW; ++w2) {
+        const int t = wtot[w2];
+        before += w2 < warp ? t : 0;
+        total += t;
+    }
+    const int base = before + x - n;  // this thread's first slot in the block order
+    for (int done = 0; done < total; done += QCAP) {  // the same trip count in every thread
+        int slot = base;
         uint32_t pm = pending;
         while (pm) {
             const int e = __ffs(pm) - 1;
             pm &= pm - 1;
-            if (slot >= done && slot < done + QCAP) q[warp][slot - done] = ((uint32_t)lane << 5) | (uint32_t)e;
+            if (slot >= done && slot < done + QCAP) q[slot - done] = (uint16_t)((threadIdx.x << 5) | e);
             ++slot;
         }
-        __syncwarp();
+        __syncthreads();
         const int nq = total - done < QCAP ? total - done : QCAP;
-        for (int t = lane; t < nq; t += 32) {
-            const uint32_t d = q[warp][t];
-            const int owner = wbase + (int)(d >> 5);
+        for (int t = threadIdx.x; t < nq; t += THREADS) {
+            const uint32_t d = q[t];
+            const int owner = (int)(d >> 5);
             sweep_task<MAXM, C>(P, kinfo, rows + (size_t)owner * MAXM, brows + (size_t)owner * MAXM,
                                 wi[owner], we0[owner], wsh[owner], (int)(d & 31u), sink);
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -800,13 +814,8 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
                 csr_user<MAXM, MODE>(P, S, i, e0, nnz, lamf, ptl, mgl, rfix, dsum, psum, x_bits, sink);
             }
         }
-        if constexpr (MODE != MODE_STATE && MAXM <= 16) {
-            // all warps of the block sweep at the same time, so the sweep code
-            // and the per-user code do not compete for the instruction cache
-            __syncthreads();
-            warp_sweeps<MAXM, C, THREADS>(P, kinfo, rows, i, e0, shm, pending, sink);
-            __syncthreads();
-        }
+        if constexpr (MODE != MODE_STATE && MAXM <= 16)
+            block_sweeps<MAXM, C, THREADS>(P, kinfo, rows, i, e0, shm, pending, sink);
         if constexpr (C == 0) __syncthreads();
     }
 }

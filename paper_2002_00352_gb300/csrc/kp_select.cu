@@ -321,6 +321,8 @@ __global__ void batch_select_kernel(BatchDev B, const double *lam, double *lam_n
     select_body(sP, sS, (int)(blockIdx.x - ko), lam + ko, lam_next + ko, round);
 }
 
+constexpr int BWD_USERS = 256;
+
 __global__ void backward_kernel(int64_t N, int M, int W, int K, const double *lam,
                                 const uint32_t *x_bits, const double *R, const double *B,
                                 const double *upstream, double *grad_lambda, float *grad_p,
@@ -333,14 +335,24 @@ __global__ void backward_kernel(int64_t N, int M, int W, int K, const double *la
         }
     }
     if (!grad_p) return;
+    // grad_p = up * x*: chunks of BWD_USERS users, their items written by
+    // consecutive threads (coalesced); the user of an item from 32-bit
+    // arithmetic (a float reciprocal, corrected to the exact quotient)
     const float upf = (float)up;
-    const int64_t total = N * (int64_t)M;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
-        const int64_t i = q / M;
-        const int j = (int)(q - i * M);
-        const uint32_t wd = __ldg(x_bits + i * W + (j >> 5));
-        grad_p[q] = ((wd >> (j & 31)) & 1u) ? upf : 0.f;
+    const float invM = 1.0f / (float)M;
+    for (int64_t i0 = (int64_t)blockIdx.x * BWD_USERS; i0 < N; i0 += (int64_t)gridDim.x * BWD_USERS) {
+        const int nu = (int)(N - i0 < BWD_USERS ? N - i0 : BWD_USERS);
+        const int ne = nu * M;
+        const uint32_t *xw = x_bits + i0 * W;
+        float *gp = grad_p + i0 * M;
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+            int u = (int)((float)e * invM);
+            if (u * M > e) --u;
+            if ((u + 1) * M <= e) ++u;
+            const int j = e - u * M;
+            const uint32_t wd = __ldg(xw + (size_t)u * W + (j >> 5));
+            gp[e] = ((wd >> (j & 31)) & 1u) ? upf : 0.f;
+        }
     }
 }
 
@@ -500,8 +512,7 @@ cudaError_t launch_backward(const Params &P, const double *lambda, const uint32_
                             const double *R, const double *upstream, double *grad_lambda,
                             float *grad_p, double *grad_B, cudaStream_t st) {
     const int sms = sm_count();
-    const int64_t total = P.N * (int64_t)P.M;
-    int64_t blocks = (total + 255) / 256;
+    int64_t blocks = (P.N + BWD_USERS - 1) / BWD_USERS;
     const int64_t cap = (int64_t)sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
