@@ -422,29 +422,31 @@ __device__ __forceinline__ uint32_t full_sets(uint32_t S, const Tree &t) {
 }
 
 // Weakest member of the fixed lines CF (ties: the higher index is weaker);
-// ybit = its bit (0 if CF is empty).
-template <int MAXM>
-__device__ __forceinline__ float weakest(const float (&w)[MAXM], uint32_t CF, uint32_t &ybit) {
+// ybit = its bit (0 if CF is empty).  w = the user's p~ row (shared memory);
+// CF holds a few selected items, so the loop visits only them.
+__device__ __forceinline__ float weakest(const float *w, uint32_t CF, uint32_t &ybit) {
     float wmin = FLT_MAX;
-    int y = 0;
-#pragma unroll
-    for (int j = 0; j < MAXM; ++j)
-        if (((CF >> j) & 1u) && w[j] <= wmin) {
-            wmin = w[j];
-            y = j;
+    uint32_t yb = 0u;
+    while (CF) {
+        const int j = __ffs(CF) - 1;
+        CF &= CF - 1;
+        const float v = w[j];
+        if (v <= wmin) {
+            wmin = v;
+            yb = 1u << j;
         }
-    ybit = CF ? 1u << y : 0u;
+    }
+    ybit = yb;
     return wmin;
 }
 
 // lambda_k at which a moving line (weight A - lambda_k s, path ip) enters the
 // selection S (full sets `full`), whose circuit holds fixed lines and possibly
 // the moving line ob (weight Ao - lambda_k so); rem = the member it replaces.
-// Branch-free: every candidate is computed and the valid one selected.
-template <int MAXM>
-__device__ __forceinline__ float entry_time(const float (&w)[MAXM], const Tree &t, uint32_t S,
-                                            uint32_t full, uint32_t ip, float A, float s, uint32_t ob,
-                                            float Ao, float so, uint32_t &rem) {
+// Branch-free apart from the short loop over the circuit's fixed members.
+__device__ __forceinline__ float entry_time(const float *w, const Tree &t, uint32_t S, uint32_t full,
+                                            uint32_t ip, float A, float s, uint32_t ob, float Ao, float so,
+                                            uint32_t &rem) {
     const uint32_t fm = ip & full;
     const uint32_t Cm = fm ? S & (uint32_t)t.items[__ffs(fm) - 1] : 0u;
     uint32_t ybit;
@@ -460,13 +462,13 @@ __device__ __forceinline__ float entry_time(const float (&w)[MAXM], const Tree &
 // straight-line predicated code: the first line enters, the second enters
 // (possibly overtaking the first), and an overtaken first line re-enters; the
 // line with the larger slope is never overtaken, so there is no fourth event.
-// ki = (lambda_k^t, window) of knapsack k.
-template <int MAXM, class Sink>
-__device__ __forceinline__ void pair_sweep(const float (&w)[MAXM], uint32_t SF, int ia, float sa,
-                                           int ib, float sb, const float4 &ki, const Tree &t, int k,
-                                           Sink &sink) {
+// w = the user's p~ row at lambda^t (shared memory); ki = (lambda_k^t,
+// window) of knapsack k.
+template <class Sink>
+__device__ __forceinline__ void pair_sweep(const float *w, uint32_t SF, int ia, float sa, int ib,
+                                           float sb, const float4 &ki, const Tree &t, int k, Sink &sink) {
     const float lamk = ki.x;
-    const float Aa = fmaf(lamk, sa, pick(w, ia)), Ab = fmaf(lamk, sb, pick(w, ib));
+    const float Aa = fmaf(lamk, sa, w[ia]), Ab = fmaf(lamk, sb, w[ib]);
     const uint32_t ipa = t.ipath[ia], ipb = t.ipath[ib];
     uint32_t full = full_sets(SF, t), ra, rb;
     float ea = entry_time(w, t, SF, full, ipa, Aa, sa, 0u, 0.f, 0.f, ra);

@@ -661,8 +661,8 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
     float sl[2] = {0.f, 0.f};
     int nj = 0;
     uint32_t J = 0;
-    uint32_t r = shm;
-    while (r) {  // entries of knapsack k are among the shared entries
+    uint32_t r = shm & ~((1u << e) - 1u);  // e is the first entry of knapsack k
+    while (r && nj < 2) {  // the other entry of knapsack k is a later shared entry
         const int f = __ffs(r) - 1;
         r &= r - 1;
         if (kid[f] != k) continue;
@@ -685,13 +685,11 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
         ++nj;
         J |= 1u << j2;
     }
-    float w[MAXM];
     uint32_t bt[MAXM], pos = 0;
 #pragma unroll
     for (int j2 = 0; j2 < MAXM; ++j2) {
-        w[j2] = prow[j2];
         bt[j2] = brow[j2];
-        if (j2 < M && w[j2] > 0.f) pos |= 1u << j2;
+        if (j2 < M && prow[j2] > 0.f) pos |= 1u << j2;
     }
     // selection among the fixed lines: Algorithm 1 over pos minus J with the
     // owner's rank masks
@@ -705,7 +703,7 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
             if (((inl >> j) & 1u) && __popc(bt[j] & inl) >= cap) drop |= 1u << j;
         SF &= ~drop;
     }
-    if (nj == 2) pair_sweep<MAXM>(w, SF, it[0], sl[0], it[1], sl[1], kinfo[k], T, k, sink);
+    if (nj == 2) pair_sweep(prow, SF, it[0], sl[0], it[1], sl[1], kinfo[k], T, k, sink);
 }
 
 // The sweeps of a block's users are pooled and dealt to its threads (about

@@ -335,24 +335,35 @@ __global__ void backward_kernel(int64_t N, int M, int W, int K, const double *la
         }
     }
     if (!grad_p) return;
-    // grad_p = up * x*: chunks of BWD_USERS users, their items written by
-    // consecutive threads (coalesced); the user of an item from 32-bit
-    // arithmetic (a float reciprocal, corrected to the exact quotient)
+    // grad_p = up * x*: a chunk of BWD_USERS users (one per thread) is expanded
+    // into shared memory, then written out with 16-byte stores by consecutive
+    // threads (each chunk starts 16-byte aligned when grad_p does)
+    extern __shared__ __align__(16) float stage[];  // [BWD_USERS * M]
     const float upf = (float)up;
-    const float invM = 1.0f / (float)M;
+    const bool vec = (reinterpret_cast<uintptr_t>(grad_p) & 15u) == 0;
     for (int64_t i0 = (int64_t)blockIdx.x * BWD_USERS; i0 < N; i0 += (int64_t)gridDim.x * BWD_USERS) {
         const int nu = (int)(N - i0 < BWD_USERS ? N - i0 : BWD_USERS);
         const int ne = nu * M;
-        const uint32_t *xw = x_bits + i0 * W;
-        float *gp = grad_p + i0 * M;
-        for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-            int u = (int)((float)e * invM);
-            if (u * M > e) --u;
-            if ((u + 1) * M <= e) ++u;
-            const int j = e - u * M;
-            const uint32_t wd = __ldg(xw + (size_t)u * W + (j >> 5));
-            gp[e] = ((wd >> (j & 31)) & 1u) ? upf : 0.f;
+        if ((int)threadIdx.x < nu) {
+            const uint32_t *xw = x_bits + (i0 + threadIdx.x) * W;
+            float *row = stage + threadIdx.x * M;
+            uint32_t wd = 0u;
+            for (int j = 0; j < M; ++j) {
+                if ((j & 31) == 0) wd = __ldg(xw + (j >> 5));
+                row[j] = ((wd >> (j & 31)) & 1u) ? upf : 0.f;
+            }
         }
+        __syncthreads();
+        float *gp = grad_p + i0 * M;
+        if (vec) {
+            const int n4 = ne >> 2;
+            for (int q = threadIdx.x; q < n4; q += blockDim.x)
+                reinterpret_cast<float4 *>(gp)[q] = reinterpret_cast<const float4 *>(stage)[q];
+            for (int q = (n4 << 2) + threadIdx.x; q < ne; q += blockDim.x) gp[q] = stage[q];
+        } else {
+            for (int q = threadIdx.x; q < ne; q += blockDim.x) gp[q] = stage[q];
+        }
+        __syncthreads();
     }
 }
 
@@ -516,8 +527,15 @@ cudaError_t launch_backward(const Params &P, const double *lambda, const uint32_
     const int64_t cap = (int64_t)sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    backward_kernel<<<(int)blocks, 256, 0, st>>>(P.N, P.M, P.W, P.K, lambda, x_bits, R, P.B, upstream,
-                                                 grad_lambda, grad_p, grad_B);
+    const size_t smem = (size_t)BWD_USERS * P.M * sizeof(float);  // at most 64 KB (M <= 64)
+    static bool attr = false;  // once, before any stream capture
+    if (!attr) {
+        cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)BWD_USERS * KP_MAX_M * sizeof(float)));
+        attr = true;
+    }
+    backward_kernel<<<(int)blocks, BWD_USERS, smem, st>>>(P.N, P.M, P.W, P.K, lambda, x_bits, R, P.B,
+                                                          upstream, grad_lambda, grad_p, grad_B);
     return cudaGetLastError();
 }
 
