@@ -559,10 +559,13 @@ __device__ __forceinline__ float breakpoint_value(float lamk, float margin, floa
 // ---------------------------------------------------------------------------
 // emission sinks
 // ---------------------------------------------------------------------------
-// First pass: exact masses above / inside / below the window, and the
-// breakpoints inside the window buffered.
+// First pass: exact masses above / inside / below the window, each split by
+// whether the breakpoint lies above lambda_k^t (their sum over the regions is
+// the user's k-consumption at lambda^t), and the breakpoints inside the window
+// buffered.
 struct WindowSink {
-    unsigned long long *reg3;  // [K][3] (shared)
+    unsigned long long *reg6;  // [K][3][2] (shared): region (above, inside, below the
+                               // window) x (v1 > lambda_k^t)
     const float4 *kinfo;       // [K] (shared): lambda_k (f32), window low, window high (exclusive)
     uint32_t *bcnt;            // [K] buffer fill of this block (shared)
     uint2 *buf;
@@ -573,7 +576,7 @@ struct WindowSink {
                                             unsigned long long m) {
         if (!(v1 > 0.f)) return;
         const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-        shared_add_u64(&reg3[3 * k + r], m);
+        shared_add_u64(&reg6[6 * k + 2 * r + (v1 > ki.x ? 1 : 0)], m);
         if (r == 1) {
             const uint32_t slot = shared_inc_u32(&bcnt[k]);
             if (slot < (uint32_t)cap_kb)
@@ -583,16 +586,17 @@ struct WindowSink {
     __device__ __forceinline__ void emit_ki(int k, const float4 &ki, float v1, float v2) {
         emit_km(k, ki, v1, v2, bmass(v2, bscale));
     }
-    // region r of a breakpoint with mass m, where emit holds (predicated)
-    __device__ __forceinline__ void region_add_if(int k, int r, unsigned long long m, bool emit) {
-        shared_add_u64_if(&reg3[3 * k + r], m, emit ? 1u : 0u);
+    // bin b = 2 * region + (v1 > lambda_k^t) of a breakpoint with mass m,
+    // where emit holds (predicated)
+    __device__ __forceinline__ void region_add_if(int k, int b, unsigned long long m, bool emit) {
+        shared_add_u64_if(&reg6[6 * k + b], m, emit ? 1u : 0u);
     }
     // predicated emission (pred false: nothing); the buffer append is a rare branch
     __device__ __forceinline__ void emit_if(int k, const float4 &ki, float v1, float v2, bool pred) {
         const bool go = pred && v1 > 0.f && v2 > 0.f;
         const unsigned long long m = bmass(v2, bscale);
         const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-        shared_add_u64_if(&reg3[3 * k + r], m, go ? 1u : 0u);
+        shared_add_u64_if(&reg6[6 * k + 2 * r + (v1 > ki.x ? 1 : 0)], m, go ? 1u : 0u);
         if (go && r == 1) buffer_add(k, v1, v2);
     }
     // a breakpoint inside the window whose mass region_add_if took

@@ -59,7 +59,7 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     s.rfix = o;
     o = align16(o + 8 * (size_t)K);
     s.reg3 = o;
-    if (mode == MODE_HIST) o = align16(o + (size_t)K * 3 * 8);
+    if (mode == MODE_HIST) o = align16(o + (size_t)K * 6 * 8);  // [K][3 regions][2]
     s.red = o;
     o = align16(o + 2 * 8 * 32);
     if (layout == KP_B_CSR) {
@@ -120,10 +120,9 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
                 S.sel[k].whi = whi;
             }
             ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, __uint_as_float(wlo), __uint_as_float(whi), 0.f);
-            unsigned long long *r3 = (unsigned long long *)(smem + L.reg3);
-            r3[3 * k] = 0ull;
-            r3[3 * k + 1] = 0ull;
-            r3[3 * k + 2] = 0ull;
+            unsigned long long *r6 = (unsigned long long *)(smem + L.reg3);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) r6[6 * k + q] = 0ull;
         } else {
             ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, 0.f, 0.f, 0.f);
         }
@@ -144,11 +143,14 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
     }
 }
 
+// r_from_bins: the consumption R at lambda^t is the mass of the block's
+// breakpoints above lambda_k^t (the breakpoint pass of regular CSR rows, which
+// takes no explicit consumption); otherwise R was accumulated per entry.
 template <int MODE>
 __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch &S,
                                                   const SmemLayout &L, unsigned char *smem,
                                                   unsigned long long dsum, unsigned long long psum,
-                                                  int blk = -1) {
+                                                  int blk = -1, bool r_from_bins = false) {
     if (blk < 0) blk = blockIdx.x - S.g_lo;
     const int K = P.K;
     uint32_t *bcnt = (uint32_t *)(smem + L.bcnt);
@@ -163,9 +165,16 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
         }
     }
     if (MODE == MODE_HIST) {
-        unsigned long long *r3 = (unsigned long long *)(smem + L.reg3);
-        for (int q = threadIdx.x; q < K * 3; q += blockDim.x)
-            if (r3[q]) atomicAdd(&S.reg3[q], r3[q]);
+        const unsigned long long *r6 = (const unsigned long long *)(smem + L.reg3);
+        for (int q = threadIdx.x; q < K * 3; q += blockDim.x) {
+            const unsigned long long m = r6[2 * q] + r6[2 * q + 1];
+            if (m) atomicAdd(&S.reg3[q], m);
+        }
+        if (r_from_bins)
+            for (int k = threadIdx.x; k < K; k += blockDim.x) {
+                const unsigned long long m = r6[6 * k + 1] + r6[6 * k + 3] + r6[6 * k + 5];
+                if (m) atomicAdd(&S.Rfix[k], m);
+            }
     }
     if (MODE != MODE_REFINE) {
         // exact fixed-point objective sums: warp reduction, one atomic per warp
@@ -183,7 +192,7 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
 __device__ __forceinline__ WindowSink make_window_sink(const Params &P, const Scratch &S,
                                                        const SmemLayout &L, unsigned char *smem) {
     WindowSink ws;
-    ws.reg3 = (unsigned long long *)(smem + L.reg3);
+    ws.reg6 = (unsigned long long *)(smem + L.reg3);
     ws.kinfo = (const float4 *)(smem + L.kinfo);
     ws.bcnt = (uint32_t *)(smem + L.bcnt);
     ws.buf = S.buf;
@@ -584,10 +593,11 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
         const uint32_t pending = shm.y;
         shared_entries = shm.x;
         if constexpr (FOLD) {
-            // Algorithm 4 Map, closed form for knapsacks only one item touches,
-            // and the consumption of the selected items: one predicated pass
-            // over the entries in registers; breakpoints that fall inside the
-            // window are buffered afterwards.
+            // Algorithm 4 Map, closed form for knapsacks only one item touches:
+            // one predicated pass over the entries in registers; breakpoints
+            // that fall inside the window are buffered afterwards.  The
+            // consumption at lambda^t is not summed here: it is the mass of
+            // the breakpoints above lambda_k^t (flush_block_state).
             uint32_t inside = 0u;
 #pragma unroll
             for (int e = 0; e < EC; ++e) {
@@ -596,11 +606,10 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 const int k = kk[e];
                 const float4 ki = kinfo[k];
                 const unsigned long long m = bmass(v, P.bscale);
-                shared_add_u64_if(&rfix[k], m, (G >> j) & 1u);
                 const float v1 = breakpoint_value(ki.x, mg[j], v);
                 const bool emit = v > 0.f && v1 > 0.f && !((shm.x >> e) & 1u);
                 const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-                sink.region_add_if(k, r, m, emit);
+                sink.region_add_if(k, 2 * r + (v1 > ki.x ? 1 : 0), m, emit);
                 inside |= (emit && r == 1) ? 1u << e : 0u;
             }
             while (inside) {
@@ -838,7 +847,7 @@ __global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch 
         NullSink ns;
         csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, ns, dsum, psum);
     }
-    flush_block_state<MODE>(P, S, L, smem, dsum, psum);
+    flush_block_state<MODE>(P, S, L, smem, dsum, psum, -1, MODE == MODE_HIST && C > 0);
 }
 
 // Knapsacks that three or more items of one user use (listed at creation; a
@@ -964,7 +973,7 @@ __global__ void __launch_bounds__(RARE_THREADS) rare_kernel(Params P, Scratch S,
         rs.blk = blk;
         run(rs);
     }
-    flush_block_state<MODE>(P, S, L, smem, 0ull, 0ull, blk);
+    flush_block_state<MODE>(P, S, L, smem, 0ull, 0ull, blk, MODE == MODE_HIST && C > 0);
 }
 
 // ------------------------------------------------------------------------------------------

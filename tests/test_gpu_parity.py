@@ -13,7 +13,7 @@ import torch
 
 import oracle
 from paper_2002_00352_gb300 import gen, kp
-from tests.gpu_util import REL_LAMBDA, compare_state, cuda_state, lam_close
+from tests.gpu_util import REL, REL_LAMBDA, TAU, compare_state, cuda_state, excused_users, lam_close
 from tests.helpers import random_laminar
 
 pytestmark = pytest.mark.gpu
@@ -79,6 +79,30 @@ def test_state_parity_sparse_config_downscaled():
 # one SCD iteration (Algorithms 3-4) at the same lambda^t
 # ---------------------------------------------------------------------------
 
+def _scd_gpu_state(prob, lam):
+    """One SCD step; also the consumption and objectives the breakpoint pass reports."""
+    lt = torch.tensor(lam, dtype=torch.float64, device="cuda")
+    ln = torch.zeros_like(lt)
+    R = torch.zeros_like(lt)
+    d = torch.zeros((), dtype=torch.float64, device="cuda")
+    pr = torch.zeros((), dtype=torch.float64, device="cuda")
+    kp.kp_scd_step(prob, lt, ln, R=R, dual_sum=d, primal_sum=pr)
+    kp.kp_device_status(prob)
+    return ln.cpu().numpy(), R.cpu().numpy(), float(d), float(pr)
+
+
+def _check_breakpoint_state(p, b, lam, R, d, pr, Ro, do, po):
+    """The breakpoint pass reports R at lambda^t as the mass of the breakpoints above
+    lambda_k^t (regular CSR rows): equal to the oracle's consumption up to the
+    contributions of users with near-tied or near-zero reduced costs."""
+    exc = excused_users(p, b, lam)
+    slackR = b[exc].sum(axis=(0, 1)) if exc.any() else np.zeros(b.shape[2])
+    assert np.all(np.abs(R - Ro) <= REL * np.abs(Ro) + slackR + 1e-9), (R, Ro)
+    s = p + np.einsum("ijk,k->ij", b, lam)
+    assert abs(d - do) <= REL * abs(do) + (2 * TAU * s[exc].sum() if exc.any() else 0.0) + 1e-9
+    assert abs(pr - po) <= REL * abs(po) + (p[exc].sum() if exc.any() else 0.0) + 1e-9
+
+
 def _scd_gpu(prob, lam):
     lt = torch.tensor(lam, dtype=torch.float64, device="cuda")
     ln = torch.zeros_like(lt)
@@ -126,7 +150,8 @@ def test_regular_csr_shared_knapsacks(M, Cn, K, seed):
         x, R, d, pr, g, _ = cuda_state(prob, torch.tensor(lam, device="cuda"))
         xo, Ro, do, po = oracle.user_pass(p, b, S, C, lam)
         compare_state(p, b, lam, x, R, d, pr, xo, Ro, do, po)
-        got = _scd_gpu(prob, lam)
+        got, Rb, db, pb = _scd_gpu_state(prob, lam)
+        _check_breakpoint_state(p, b, lam, Rb, db, pb, Ro, do, po)
         want, _, _ = oracle.scd_step(p, b, S, C, lam, B)
         assert np.all(lam_close(got, want)), (trial, got, want)
 
@@ -154,7 +179,9 @@ def test_scd_step_sparse_downscaled():
     B = inst.B.cpu().numpy()
     lam = np.zeros(inst.K)
     for t in range(4):
-        got = _scd_gpu(prob, lam)
+        got, Rb, db, pb = _scd_gpu_state(prob, lam)
+        _, Ro, do, po = oracle.user_pass(p, b, inst.S, inst.C, lam, want_x=False)
+        _check_breakpoint_state(p, b, lam, Rb, db, pb, Ro, do, po)
         want, _, _ = oracle.scd_step(p, b, inst.S, inst.C, lam, B)
         frac_ok = lam_close(got, want).mean()
         assert frac_ok == 1.0, (t, frac_ok, np.max(np.abs(got - want) / np.maximum(want, 1e-12)))
