@@ -93,8 +93,8 @@ struct Scratch {
     SelK *sel;                        // [K]
     Counters *ctr;
     uint2 *shmask;                    // [N] CSR: .x entries whose knapsack another item of the user
-                                      // also uses, .y the first entry of every knapsack exactly two
-                                      // items of the user use
+                                      // also uses, .y up to PAIRS_MAX knapsacks exactly two items of
+                                      // the user use (pair_first / pair_second / pair_count)
     const unsigned long long *rare;   // [nrare] CSR: (user << 5) | first entry, for the knapsacks
                                       // that three or more items of one user use
     int64_t nrare;
@@ -118,6 +118,14 @@ struct BatchDev {
     int64_t ntiles;
     int32_t count;
 };
+
+// Knapsacks used by exactly two items of a user, listed in shmask.y: up to
+// PAIRS_MAX (first entry, second entry) pairs of 5-bit entry indices, the count
+// in the top two bits.  Further ones go to the rare-knapsack list.
+constexpr int PAIRS_MAX = 3;
+__host__ __device__ inline int pair_count(uint32_t y) { return (int)(y >> 30); }
+__host__ __device__ inline int pair_first(uint32_t y, int t) { return (int)((y >> (10 * t)) & 31u); }
+__host__ __device__ inline int pair_second(uint32_t y, int t) { return (int)((y >> (10 * t + 5)) & 31u); }
 
 // Fixed-point unit 2^-s of the b masses: the mass round(b * 2^s) of one entry
 // stays below 2^30 (one 32-bit conversion per entry) and every per-knapsack

@@ -304,10 +304,10 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
     // breakpoint is lambda_k + margin_j / b_jk.
     item_thresholds(pt, M, w, T, mg);
     for (int j = 0; j < M; ++j) mg[j] = pt[j] - mg[j];
-    uint32_t pending = 0;  // first entries of the knapsacks shared by several items
+    uint32_t pending = 0;  // first entries of the knapsacks two items use
     if (nnz <= 32) {
         const uint2 shm = S.shmask[i];
-        pending = shm.y;
+        for (int t = 0; t < pair_count(shm.y); ++t) pending |= 1u << pair_first(shm.y, t);
         int e = 0;
         for (int j = 0; j < M; ++j) {
             const int c = nzr[j];
@@ -652,48 +652,32 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
     }
 }
 
-// One shared-knapsack sweep (a knapsack exactly two items of the owner use;
-// the others have a kernel of their own, rare_kernel): the owner's p~ row and
-// rank masks are in shared memory, the two slopes b_jk are found among the
-// owner's shared entries (shm).
+// One shared-knapsack sweep (a knapsack exactly two items of the owner use,
+// entries e and e2, listed at creation; the others have a kernel of their
+// own, rare_kernel): the owner's p~ row and rank masks are in shared memory.
 template <int MAXM, int C, class Sink>
 __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo, const float *prow,
-                                           const uint32_t *brow, int64_t i, int64_t e0, uint32_t shm,
-                                           int e, Sink &sink) {
+                                           const uint32_t *brow, int64_t i, int64_t e0, int e, int e2,
+                                           Sink &sink) {
     const int M = P.M;
     const Tree &T = P.tree;
     const uint8_t *nzr = P.innz + (size_t)i * M;
     const float *val = P.val + e0;
     const int16_t *kid = P.kidx + e0;
     const int k = kid[e];
-    int it[2] = {0, 0};
-    float sl[2] = {0.f, 0.f};
-    int nj = 0;
-    uint32_t J = 0;
-    uint32_t r = shm & ~((1u << e) - 1u);  // e is the first entry of knapsack k
-    while (r && nj < 2) {  // the other entry of knapsack k is a later shared entry
-        const int f = __ffs(r) - 1;
-        r &= r - 1;
-        if (kid[f] != k) continue;
-        int j2;
-        if constexpr (C > 0) {
-            j2 = f / C;
-        } else {
-            int acc = 0;
-            j2 = 0;
-            while (acc + (int)nzr[j2] <= f) acc += nzr[j2++];
-        }
-        const float vv = __ldg(val + f);
-        if (nj == 0) {
-            it[0] = j2;
-            sl[0] = vv;
-        } else {
-            it[1] = j2;
-            sl[1] = vv;
-        }
-        ++nj;
-        J |= 1u << j2;
+    const float sa = __ldg(val + e), sb = __ldg(val + e2);
+    int ia, ib;
+    if constexpr (C > 0) {
+        ia = e / C;
+        ib = e2 / C;
+    } else {
+        int acc = 0, j2 = 0;
+        while (acc + (int)nzr[j2] <= e) acc += nzr[j2++];
+        ia = j2;
+        while (acc + (int)nzr[j2] <= e2) acc += nzr[j2++];
+        ib = j2;
     }
+    const uint32_t J = (1u << ia) | (1u << ib);
     uint32_t bt[MAXM], pos = 0;
 #pragma unroll
     for (int j2 = 0; j2 < MAXM; ++j2) {
@@ -712,7 +696,7 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
             if (((inl >> j) & 1u) && __popc(bt[j] & inl) >= cap) drop |= 1u << j;
         SF &= ~drop;
     }
-    if (nj == 2) pair_sweep(prow, SF, it[0], sl[0], it[1], sl[1], kinfo[k], T, k, sink);
+    pair_sweep(prow, SF, ia, sa, ib, sb, kinfo[k], T, k, sink);
 }
 
 // The sweeps of a block's users are pooled and dealt to its threads (about
@@ -727,14 +711,14 @@ __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinf
                                              Sink &sink) {
     constexpr int QCAP = 2 * THREADS;
     constexpr int NW = THREADS / 32;
-    static_assert(THREADS <= 2048, "task records hold the owner in 11 bits");
+    static_assert(THREADS <= 16384, "task records hold the owner in 14 bits");
     __shared__ uint16_t q[QCAP];
     __shared__ long long wi[THREADS], we0[THREADS];
-    __shared__ uint32_t wsh[THREADS];
+    __shared__ uint32_t wpy[THREADS];
     __shared__ int wtot[NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t *brows = reinterpret_cast<const uint32_t *>(rows + 2 * (size_t)THREADS * MAXM);
-    const int n = __popc(pending);
+    const int n = pair_count(pending);
     int x = n;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -745,7 +729,7 @@ __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinf
     if (pending) {
         wi[threadIdx.x] = i;
         we0[threadIdx.x] = e0;
-        wsh[threadIdx.x] = shm;
+        wpy[threadIdx.x] = pending;
     }
     __syncthreads();
     int before = 0, total = 0;
@@ -757,21 +741,18 @@ __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinf
     }
     const int base = before + x - n;  // this thread's first slot in the block order
     for (int done = 0; done < total; done += QCAP) {  // the same trip count in every thread
-        int slot = base;
-        uint32_t pm = pending;
-        while (pm) {
-            const int e = __ffs(pm) - 1;
-            pm &= pm - 1;
-            if (slot >= done && slot < done + QCAP) q[slot - done] = (uint16_t)((threadIdx.x << 5) | e);
-            ++slot;
+        for (int t = 0; t < n; ++t) {
+            const int slot = base + t;
+            if (slot >= done && slot < done + QCAP) q[slot - done] = (uint16_t)((threadIdx.x << 2) | t);
         }
         __syncthreads();
         const int nq = total - done < QCAP ? total - done : QCAP;
         for (int t = threadIdx.x; t < nq; t += THREADS) {
             const uint32_t d = q[t];
-            const int owner = (int)(d >> 5);
+            const int owner = (int)(d >> 2), pt = (int)(d & 3u);
+            const uint32_t py = wpy[owner];
             sweep_task<MAXM, C>(P, kinfo, rows + (size_t)owner * MAXM, brows + (size_t)owner * MAXM,
-                                wi[owner], we0[owner], wsh[owner], (int)(d & 31u), sink);
+                                wi[owner], we0[owner], pair_first(py, pt), pair_second(py, pt), sink);
         }
         __syncthreads();
     }

@@ -437,10 +437,10 @@ int sm_count() {
 
 // For every user with at most 32 entries: bit e of .x set iff entry e has
 // b > 0 and another item of the same user has an entry with the same knapsack
-// and b > 0; bit e of .y set iff entry e is the first entry of a knapsack that
-// exactly two items of the user use.  Knapsacks used by three or more items
-// are counted in *count and, if rare != nullptr, listed as (user << 5) | first
-// entry (at most cap of them).
+// and b > 0; .y lists up to PAIRS_MAX knapsacks that exactly two items of the
+// user use as (first entry, second entry).  Knapsacks used by three or more
+// items, and pairs beyond PAIRS_MAX, are counted in *count and, if
+// rare != nullptr, listed as (user << 5) | first entry (at most cap of them).
 __global__ void shmask_kernel(Params P, uint2 *shmask, unsigned long long *rare, int64_t cap,
                               unsigned long long *count) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -457,22 +457,26 @@ __global__ void shmask_kernel(Params P, uint2 *shmask, unsigned long long *rare,
             const int c = P.innz[i * P.M + j];
             for (int q = 0; q < c && e < 32; ++q) owner[e++] = j;
         }
-        uint32_t m = 0, first = 0;
+        uint32_t m = 0, pairs = 0;
+        int np = 0;
         for (int a = 0; a < (int)nnz; ++a) {
             if (!(P.val[e0 + a] > 0.f)) continue;
             const int ka = P.kidx[e0 + a];
             int users = 1;  // entries of knapsack ka with b > 0 (one per item)
+            int partner = -1;
             bool earlier = false;
             for (int b = 0; b < (int)nnz; ++b)
                 if (b != a && P.kidx[e0 + b] == ka && P.val[e0 + b] > 0.f) {
                     if (owner[b] != owner[a]) ++users;
                     if (b < a) earlier = true;
+                    partner = b;
                 }
             if (users >= 2) {
                 m |= 1u << a;
                 if (!earlier) {
-                    if (users == 2) {
-                        first |= 1u << a;
+                    if (users == 2 && np < PAIRS_MAX) {
+                        pairs |= ((uint32_t)a | ((uint32_t)partner << 5)) << (10 * np);
+                        ++np;
                     } else {
                         const unsigned long long slot = atomicAdd(count, 1ull);
                         if (rare && (int64_t)slot < cap) rare[slot] = ((unsigned long long)i << 5) | (unsigned)a;
@@ -480,7 +484,7 @@ __global__ void shmask_kernel(Params P, uint2 *shmask, unsigned long long *rare,
                 }
             }
         }
-        shmask[i] = make_uint2(m, first);
+        shmask[i] = make_uint2(m, pairs | ((uint32_t)np << 30));
     }
 }
 
