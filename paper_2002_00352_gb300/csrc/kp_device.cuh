@@ -488,15 +488,16 @@ __device__ __forceinline__ void pair_sweep(const float *w, uint32_t SF, int ia, 
     e2 = fminf(e2, e1);
     const bool ok2 = ok1 && Ao > 0.f && e2 > 0.f;
     const bool over = ok2 && ro == bf;  // the second line overtakes the first
-    S = (S & ~bf) | bo;
-    full = full_sets(S, t);
-    uint32_t r3;
-    float e3 = entry_time(w, t, S, full, ipf, Af, sf, bo, Ao, so, r3);
-    e3 = fminf(e3, e2);
-    const bool ok3 = over && e3 > 0.f;
     sink.emit_if(k, ki, e1, sf, ok1);
     sink.emit_if(k, ki, e2, over ? so - sf : so, ok2);
-    sink.emit_if(k, ki, e3, sf, ok3);
+    if (over) {  // rare: a warp skips this unless one of its lanes needs it
+        S = (S & ~bf) | bo;
+        full = full_sets(S, t);
+        uint32_t r3;
+        float e3 = entry_time(w, t, S, full, ipf, Af, sf, bo, Ao, so, r3);
+        e3 = fminf(e3, e2);
+        sink.emit_if(k, ki, e3, sf, e3 > 0.f);
+    }
 }
 
 // The walk state (counters, full sets) of a given selection.
