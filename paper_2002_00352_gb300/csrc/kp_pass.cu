@@ -609,7 +609,11 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 const float v1 = breakpoint_value(ki.x, mg[j], v);
                 const bool emit = v > 0.f && v1 > 0.f && !((shm.x >> e) & 1u);
                 const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-                sink.region_add_if(k, 2 * r + (v1 > ki.x ? 1 : 0), m, emit);
+                // breakpoints below both the window and lambda_k^t add to no
+                // mass the selection reads (the select then learns whether
+                // everything fits from a re-run over the range below)
+                const bool above_t = v1 > ki.x;
+                sink.region_add_if(k, 2 * r + (above_t ? 1 : 0), m, emit && (r != 2 || above_t));
                 inside |= (emit && r == 1) ? 1u << e : 0u;
             }
             while (inside) {

@@ -205,8 +205,11 @@ __device__ __forceinline__ void select_body(const Params &P, Scratch &S, int k, 
             S.reg3[3 * k + 1] = 0ull;
             S.reg3[3 * k + 2] = 0ull;
         }
+        // the regular-CSR breakpoint pass leaves out of Bl the breakpoints
+        // below both the window and lambda_k^t: the total is then unknown here
+        const bool below_known = !(P.layout == KP_B_CSR && P.creg > 0 && P.M <= 16);
         const unsigned long long total = A + W + Bl;
-        if (total <= Bfix) {  // the whole mass fits: lambda_k = 0
+        if (below_known && total <= Bfix) {  // the whole mass fits: lambda_k = 0
             if (threadIdx.x == 0) {
                 resolved(sk, k, 0u, lam_t, lam_next);
                 atomicAdd(&S.ctr->stats[1], 1ull);
@@ -265,10 +268,15 @@ __device__ __forceinline__ void select_body(const Params &P, Scratch &S, int k, 
     }
     __syncthreads();
     const int pick = s_pick;
-    if (pick < 0) {  // inconsistent: the range does not hold the crossing
+    if (pick < 0) {
         if (threadIdx.x == 0) {
-            atomicOr(&S.ctr->status, 1 << KP_ESTATE);
-            resolved(sk, k, sk.lo, lam_t, lam_next);
+            if (sk.lo <= 1u) {  // the range reaches down to 0 and everything fits: lambda_k = 0
+                resolved(sk, k, 0u, lam_t, lam_next);
+                atomicAdd(&S.ctr->stats[1], 1ull);
+            } else {  // inconsistent: the range does not hold the crossing
+                atomicOr(&S.ctr->status, 1 << KP_ESTATE);
+                resolved(sk, k, sk.lo, lam_t, lam_next);
+            }
             S.sel[k] = sk;
         }
         return;
