@@ -403,7 +403,7 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
 // user's p~ row is then left in prow.
 template <int MAXM, int C, int MODE, class Sink>
 __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch &S, int64_t i,
-                                                  int64_t e0, const float4 *kinfo,
+                                                  int64_t e0, const float *lamf, const float4 *kinfo,
                                                   unsigned long long *rfix, unsigned long long &dsum,
                                                   unsigned long long &psum, uint32_t *x_bits,
                                                   Sink &sink, float *prow, uint32_t &shared_entries) {
@@ -481,7 +481,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
         for (int j = 0; j < MAXM; ++j) {
             float acc = pt[j];
 #pragma unroll
-            for (int q = 0; q < C; ++q) acc = fmaf(-kinfo[kk[j * C + q]].x, vv[j * C + q], acc);
+            for (int q = 0; q < C; ++q) acc = fmaf(-lamf[kk[j * C + q]], vv[j * C + q], acc);
             pt[j] = acc;
         }
     } else {
@@ -489,7 +489,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) {
             float acc = pt[j];
-            for (int q = 0; q < cnt[j]; ++q, ++e) acc = fmaf(-kinfo[kid[e]].x, __ldg(val + e), acc);
+            for (int q = 0; q < cnt[j]; ++q, ++e) acc = fmaf(-lamf[kid[e]], __ldg(val + e), acc);
             pt[j] = acc;
         }
     }
@@ -796,7 +796,7 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
             bool done = false;
             if constexpr (MAXM <= 16) {
                 if (nnz <= 32) {
-                    pending = csr_user_fast<MAXM, C, MODE>(P, S, i, e0, kinfo, rfix, dsum, psum, x_bits,
+                    pending = csr_user_fast<MAXM, C, MODE>(P, S, i, e0, lamf, kinfo, rfix, dsum, psum, x_bits,
                                                            sink, rows + (size_t)threadIdx.x * MAXM, shm);
                     done = true;
                 }
