@@ -565,8 +565,9 @@ __device__ __forceinline__ float breakpoint_value(float lamk, float margin, floa
 // the user's k-consumption at lambda^t), and the breakpoints inside the window
 // buffered.
 struct WindowSink {
-    unsigned long long *reg6;  // [K][3][2] (shared): region (above, inside, below the
-                               // window) x (v1 > lambda_k^t)
+    unsigned long long *reg6;  // [3][2][K] (shared): region (above, inside, below the
+                               // window) x (v1 > lambda_k^t), knapsack fastest (banks)
+    int K;
     const float4 *kinfo;       // [K] (shared): lambda_k (f32), window low, window high (exclusive)
     uint32_t *bcnt;            // [K] buffer fill of this block (shared)
     uint2 *buf;
@@ -577,7 +578,7 @@ struct WindowSink {
                                             unsigned long long m) {
         if (!(v1 > 0.f)) return;
         const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-        shared_add_u64(&reg6[6 * k + 2 * r + (v1 > ki.x ? 1 : 0)], m);
+        shared_add_u64(&reg6[(2 * r + (v1 > ki.x ? 1 : 0)) * K + k], m);
         if (r == 1) {
             const uint32_t slot = shared_inc_u32(&bcnt[k]);
             if (slot < (uint32_t)cap_kb)
@@ -590,14 +591,14 @@ struct WindowSink {
     // bin b = 2 * region + (v1 > lambda_k^t) of a breakpoint with mass m,
     // where emit holds (predicated)
     __device__ __forceinline__ void region_add_if(int k, int b, unsigned long long m, bool emit) {
-        shared_add_u64_if(&reg6[6 * k + b], m, emit ? 1u : 0u);
+        shared_add_u64_if(&reg6[b * K + k], m, emit ? 1u : 0u);
     }
     // predicated emission (pred false: nothing); the buffer append is a rare branch
     __device__ __forceinline__ void emit_if(int k, const float4 &ki, float v1, float v2, bool pred) {
         const bool go = pred && v1 > 0.f && v2 > 0.f;
         const unsigned long long m = bmass(v2, bscale);
         const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-        shared_add_u64_if(&reg6[6 * k + 2 * r + (v1 > ki.x ? 1 : 0)], m, go ? 1u : 0u);
+        shared_add_u64_if(&reg6[(2 * r + (v1 > ki.x ? 1 : 0)) * K + k], m, go ? 1u : 0u);
         if (go && r == 1) buffer_add(k, v1, v2);
     }
     // a breakpoint inside the window whose mass region_add_if took

@@ -122,7 +122,7 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
             ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, __uint_as_float(wlo), __uint_as_float(whi), 0.f);
             unsigned long long *r6 = (unsigned long long *)(smem + L.reg3);
 #pragma unroll
-            for (int q = 0; q < 6; ++q) r6[6 * k + q] = 0ull;
+            for (int q = 0; q < 6; ++q) r6[q * K + k] = 0ull;
         } else {
             ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, 0.f, 0.f, 0.f);
         }
@@ -166,13 +166,14 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
     }
     if (MODE == MODE_HIST) {
         const unsigned long long *r6 = (const unsigned long long *)(smem + L.reg3);
-        for (int q = threadIdx.x; q < K * 3; q += blockDim.x) {
-            const unsigned long long m = r6[2 * q] + r6[2 * q + 1];
+        for (int q = threadIdx.x; q < K * 3; q += blockDim.x) {  // q = 3k + r
+            const int k = q / 3, r = q - 3 * k;
+            const unsigned long long m = r6[(2 * r) * K + k] + r6[(2 * r + 1) * K + k];
             if (m) atomicAdd(&S.reg3[q], m);
         }
         if (r_from_bins)
             for (int k = threadIdx.x; k < K; k += blockDim.x) {
-                const unsigned long long m = r6[6 * k + 1] + r6[6 * k + 3] + r6[6 * k + 5];
+                const unsigned long long m = r6[1 * K + k] + r6[3 * K + k] + r6[5 * K + k];
                 if (m) atomicAdd(&S.Rfix[k], m);
             }
     }
@@ -193,6 +194,7 @@ __device__ __forceinline__ WindowSink make_window_sink(const Params &P, const Sc
                                                        const SmemLayout &L, unsigned char *smem) {
     WindowSink ws;
     ws.reg6 = (unsigned long long *)(smem + L.reg3);
+    ws.K = P.K;
     ws.kinfo = (const float4 *)(smem + L.kinfo);
     ws.bcnt = (uint32_t *)(smem + L.bcnt);
     ws.buf = S.buf;
