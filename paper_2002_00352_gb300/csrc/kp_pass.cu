@@ -64,7 +64,8 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     o = align16(o + 2 * 8 * 32);
     if (layout == KP_B_CSR) {
         s.rows = o;  // per thread: p~ row and rank masks (for shared-knapsack sweeps), margin row
-        if (mode != MODE_STATE) o = align16(o + 3 * 4 * (size_t)threads * maxm);
+        // (rows of the register path only: M <= 16)
+        if (mode != MODE_STATE && maxm <= 16) o = align16(o + 3 * 4 * (size_t)threads * maxm);
         s.tile_p = s.tile_b = s.selm = o;
     } else {
         s.tile_p = o;
@@ -651,7 +652,9 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
 #pragma unroll
             for (int j = 0; j < MAXM; ++j) {
                 prow[j] = pt[j];
-                brow[j] = beats[j];
+                // rank masks use bits 0..15 (M <= 16); the positive items ride in
+                // the high half of the first word
+                brow[j] = beats[j] | (j == 0 ? pos << 16 : 0u);
             }
         }
         return pending;
@@ -684,12 +687,11 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
         ib = j2;
     }
     const uint32_t J = (1u << ia) | (1u << ib);
-    uint32_t bt[MAXM], pos = 0;
+    static_assert(MAXM <= 16, "rank masks and the positive items share a word");
+    uint32_t bt[MAXM];
 #pragma unroll
-    for (int j2 = 0; j2 < MAXM; ++j2) {
-        bt[j2] = brow[j2];
-        if (j2 < M && prow[j2] > 0.f) pos |= 1u << j2;
-    }
+    for (int j2 = 0; j2 < MAXM; ++j2) bt[j2] = brow[j2] & 0xffffu;
+    const uint32_t pos = brow[0] >> 16;
     // selection among the fixed lines: Algorithm 1 over pos minus J with the
     // owner's rank masks
     uint32_t SF = pos & ~J;

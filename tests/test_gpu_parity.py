@@ -156,6 +156,28 @@ def test_regular_csr_shared_knapsacks(M, Cn, K, seed):
         assert np.all(lam_close(got, want)), (trial, got, want)
 
 
+@pytest.mark.parametrize("layout", ["csr", "dense"])
+def test_scd_step_parity_wide_users(layout):
+    """M = 20 and 40 items per user (beyond the register path of 16): the general
+    per-user routine and its kinetic sweeps, one SCD step and the state against the
+    oracle."""
+    for M, K, seed in ((20, 4, 31), (40, 3, 32)):
+        rng = np.random.default_rng(seed)
+        S, C = random_laminar(M, rng, max_nodes=5)
+        inst = gen.random_small(600, M, K, seed=seed, device="cuda", layout=layout, frac=0.15)
+        inst.S, inst.C = S, C
+        prob = _problem(inst)
+        p, b = _dense_np(inst)
+        B = inst.B.cpu().numpy()
+        lam = rng.uniform(0, 0.8, size=K)
+        x, R, d, pr, g, _ = cuda_state(prob, torch.tensor(lam, device="cuda"))
+        xo, Ro, do, po = oracle.user_pass(p, b, S, C, lam)
+        compare_state(p, b, lam, x, R, d, pr, xo, Ro, do, po)
+        got = _scd_gpu(prob, lam)
+        want, _, _ = oracle.scd_step(p, b, S, C, lam, B)
+        assert np.all(lam_close(got, want)), (M, got, want)
+
+
 def test_scd_trajectory_small_config():
     """N=1e4, M=10, K=5: 50 SCD iterations; each GPU step matches the oracle's step
     taken at the GPU's own lambda^t."""
