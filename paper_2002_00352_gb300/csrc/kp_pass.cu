@@ -29,6 +29,7 @@ namespace kp {
 namespace {
 
 constexpr int DENSE_TILE_BYTES = 64 * 1024;   // dense b tile
+constexpr int CSR_SETS = 2;                    // CSR user tiles per sweep phase (regular rows)
 
 struct SmemLayout {
     size_t lamf, kinfo, ckey, wwin, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, total;
@@ -37,7 +38,7 @@ struct SmemLayout {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int maxm, int threads,
-                                                  int T, int mode) {
+                                                  int T, int mode, int sets = 1) {
     SmemLayout s;
     size_t o = 0;
     s.lamf = o;
@@ -64,8 +65,8 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     o = align16(o + 2 * 8 * 32);
     if (layout == KP_B_CSR) {
         s.rows = o;  // per thread: p~ row and rank masks (for shared-knapsack sweeps), margin row
-        // (rows of the register path only: M <= 16)
-        if (mode != MODE_STATE && maxm <= 16) o = align16(o + 3 * 4 * (size_t)threads * maxm);
+        // (rows of the register path only: M <= 16; `sets` sets of them)
+        if (mode != MODE_STATE && maxm <= 16) o = align16(o + (size_t)sets * 3 * 4 * (size_t)threads * maxm);
         s.tile_p = s.tile_b = s.selm = o;
     } else {
         s.tile_p = o;
@@ -713,20 +714,29 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
 // same time, so the sweep code and the per-user code do not compete for the
 // instruction cache.  Called by every thread of the block; contains the block
 // barriers that make the owners' rows visible and protect them until done.
-template <int MAXM, int C, int THREADS, class Sink>
+template <int MAXM, int C, int THREADS, int U, class Sink>
 __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinfo, float *rows,
-                                             int64_t i, int64_t e0, uint32_t shm, uint32_t pending,
-                                             Sink &sink) {
-    constexpr int QCAP = 2 * THREADS;
+                                             const int64_t (&ii)[U], const int64_t (&ee)[U],
+                                             const uint32_t (&pend)[U], Sink &sink) {
+    constexpr int QCAP = 2 * U * THREADS;
     constexpr int NW = THREADS / 32;
-    static_assert(THREADS <= 16384, "task records hold the owner in 14 bits");
+    constexpr size_t SET = 3 * (size_t)THREADS * MAXM;  // rows of one user set
+    static_assert(U * THREADS <= 16384, "task records hold the owner in 14 bits");
     __shared__ uint16_t q[QCAP];
-    __shared__ long long wi[THREADS], we0[THREADS];
-    __shared__ uint32_t wpy[THREADS];
+    __shared__ long long wi[U * THREADS], we0[U * THREADS];
+    __shared__ uint32_t wpy[U * THREADS];
     __shared__ int wtot[NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t *brows = reinterpret_cast<const uint32_t *>(rows + 2 * (size_t)THREADS * MAXM);
-    const int n = pair_count(pending);
+    int n = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        n += pair_count(pend[u]);
+        if (pend[u]) {
+            wi[u * THREADS + threadIdx.x] = ii[u];
+            we0[u * THREADS + threadIdx.x] = ee[u];
+            wpy[u * THREADS + threadIdx.x] = pend[u];
+        }
+    }
     int x = n;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -734,11 +744,6 @@ __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinf
         if (lane >= o) x += y;
     }
     if (lane == 31) wtot[warp] = x;
-    if (pending) {
-        wi[threadIdx.x] = i;
-        we0[threadIdx.x] = e0;
-        wpy[threadIdx.x] = pending;
-    }
     __syncthreads();
     int before = 0, total = 0;
 #pragma unroll
@@ -749,18 +754,23 @@ __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinf
     }
     const int base = before + x - n;  // this thread's first slot in the block order
     for (int done = 0; done < total; done += QCAP) {  // the same trip count in every thread
-        for (int t = 0; t < n; ++t) {
-            const int slot = base + t;
-            if (slot >= done && slot < done + QCAP) q[slot - done] = (uint16_t)((threadIdx.x << 2) | t);
-        }
+        int slot = base;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            for (int t = 0; t < pair_count(pend[u]); ++t, ++slot)
+                if (slot >= done && slot < done + QCAP)
+                    q[slot - done] = (uint16_t)(((u * THREADS + threadIdx.x) << 2) | t);
         __syncthreads();
         const int nq = total - done < QCAP ? total - done : QCAP;
         for (int t = threadIdx.x; t < nq; t += THREADS) {
             const uint32_t d = q[t];
             const int owner = (int)(d >> 2), pt = (int)(d & 3u);
+            const int ou = owner / THREADS, ot = owner - ou * THREADS;
+            const float *prow = rows + ou * SET + (size_t)ot * MAXM;
+            const uint32_t *brow = reinterpret_cast<const uint32_t *>(prow + 2 * (size_t)THREADS * MAXM);
             const uint32_t py = wpy[owner];
-            sweep_task<MAXM, C>(P, kinfo, rows + (size_t)owner * MAXM, brows + (size_t)owner * MAXM,
-                                wi[owner], we0[owner], pair_first(py, pt), pair_second(py, pt), sink);
+            sweep_task<MAXM, C>(P, kinfo, prow, brow, wi[owner], we0[owner], pair_first(py, pt),
+                                pair_second(py, pt), sink);
         }
         __syncthreads();
     }
@@ -769,7 +779,7 @@ __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinf
 template <int MAXM, int C, int MODE, int THREADS, class Sink>
 __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsigned char *smem,
                                          const SmemLayout &L, uint32_t *x_bits, Sink &sink,
-                                         unsigned long long &dsum, unsigned long long &psum) {
+                                         unsigned long long &dsum, unsigned long long &psum, int sets) {
     __shared__ int s_scan[THREADS / 32];
     __shared__ long long s_base;
     const int M = P.M;
@@ -777,6 +787,36 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
     const float4 *kinfo = (const float4 *)(smem + L.kinfo);
     unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
     float *rows = (float *)(smem + L.rows);
+    if constexpr (C > 0 && MODE != MODE_STATE && MAXM <= 16) if (sets == CSR_SETS) {
+        // regular rows: CSR_SETS consecutive tiles of users per sweep phase, so
+        // the block meets its barriers once per CSR_SETS tiles (when the rows of
+        // CSR_SETS tiles fit in shared memory next to the per-knapsack state)
+        constexpr int U = CSR_SETS;
+        constexpr size_t SET = 3 * (size_t)THREADS * MAXM;
+        const int64_t step = (int64_t)gridDim.x * THREADS * U;
+        for (int64_t base = (int64_t)blockIdx.x * THREADS * U; base < P.N; base += step) {
+            int64_t ii[U], ee[U];
+            uint32_t pend[U];
+#pragma unroll 1
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = base + (int64_t)u * THREADS + threadIdx.x;
+                const int64_t e0 = P.uoff0 + i * (int64_t)(M * C);
+                uint32_t pd = 0u, shm = 0u;
+                if (i < P.N)
+                    pd = csr_user_fast<MAXM, C, MODE>(P, S, i, e0, lamf, kinfo, rfix, dsum, psum, x_bits, sink,
+                                                      rows + u * SET + (size_t)threadIdx.x * MAXM, shm);
+#pragma unroll
+                for (int v = 0; v < U; ++v)
+                    if (v == u) {
+                        ii[v] = i;
+                        ee[v] = e0;
+                        pend[v] = pd;
+                    }
+            }
+            block_sweeps<MAXM, C, THREADS, U>(P, kinfo, rows, ii, ee, pend, sink);
+        }
+        return;
+    }
     for (int64_t base = (int64_t)blockIdx.x * THREADS; base < P.N; base += (int64_t)gridDim.x * THREADS) {
         const int64_t i = base + threadIdx.x;
         const bool valid = i < P.N;
@@ -810,31 +850,34 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
                 csr_user<MAXM, MODE>(P, S, i, e0, nnz, lamf, ptl, mgl, rfix, dsum, psum, x_bits, sink);
             }
         }
-        if constexpr (MODE != MODE_STATE && MAXM <= 16)
-            block_sweeps<MAXM, C, THREADS>(P, kinfo, rows, i, e0, shm, pending, sink);
+        if constexpr (MODE != MODE_STATE && MAXM <= 16) {
+            const int64_t ii[1] = {i}, ee[1] = {e0};
+            const uint32_t pend[1] = {pending};
+            block_sweeps<MAXM, C, THREADS, 1>(P, kinfo, rows, ii, ee, pend, sink);
+        }
         if constexpr (C == 0) __syncthreads();
     }
 }
 
 template <int MAXM, int C, int MODE, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch S, const double *lam,
-                                                              uint32_t *x_bits, int round) {
+                                                              uint32_t *x_bits, int round, int sets) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
     if (MODE != MODE_STATE && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&S.ctr->stats[0], 1ull);
-    const SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, THREADS, 0, MODE);
+    const SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, THREADS, 0, MODE, sets);
     init_block_state<MODE>(P, S, lam, L, smem, round, blockIdx.x == 0);
     __syncthreads();
     unsigned long long dsum = 0ull, psum = 0ull;
     if (MODE == MODE_HIST) {
         WindowSink ws = make_window_sink(P, S, L, smem);
-        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, ws, dsum, psum);
+        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, ws, dsum, psum, sets);
     } else if (MODE == MODE_REFINE) {
         RefineSink rs = make_refine_sink(P, S, L, smem);
-        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, rs, dsum, psum);
+        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, rs, dsum, psum, sets);
     } else {
         NullSink ns;
-        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, ns, dsum, psum);
+        csr_loop<MAXM, C, MODE, THREADS>(P, S, smem, L, x_bits, ns, dsum, psum, sets);
     }
     flush_block_state<MODE>(P, S, L, smem, dsum, psum, -1, MODE == MODE_HIST && C > 0);
 }
@@ -1180,15 +1223,21 @@ cudaError_t prepare_kernel(Kern kern, int *max_dyn) {
 template <int MAXM, int C, int MODE>
 cudaError_t launch_csr(const Params &P, const Scratch &S, const double *lam, uint32_t *x_bits,
                        int round, cudaStream_t st, int *occupancy_out) {
-    SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE);
     auto kern = csr_pass_kernel<MAXM, C, MODE, CSR_THREADS>;
     static int max_dyn = -1;  // once per instantiation, before any stream capture
     cudaError_t e = prepare_kernel(kern, &max_dyn);
     if (e != cudaSuccess) return e;
+    // CSR_SETS tiles per sweep phase when their rows fit, else one
+    int sets = (C > 0 && MODE != MODE_STATE && MAXM <= 16) ? CSR_SETS : 1;
+    SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE, sets);
+    if (L.total > (size_t)max_dyn && sets > 1) {
+        sets = 1;
+        L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE, sets);
+    }
     if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
     if (occupancy_out)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, CSR_THREADS, L.total);
-    kern<<<S.G, CSR_THREADS, L.total, st>>>(P, S, lam, x_bits, round);
+    kern<<<S.G, CSR_THREADS, L.total, st>>>(P, S, lam, x_bits, round, sets);
     return cudaGetLastError();
 }
 
