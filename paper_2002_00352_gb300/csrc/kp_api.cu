@@ -392,6 +392,9 @@ kp_status kp_scd_breakpoints(kp_problem *h, const double *lambda, double *R, dou
     cudaStream_t st = (cudaStream_t)stream;
     KP_CUDA(cudaMemsetAsync(h->S.ctr, 0, offsetof(kp::Counters, status), st), "reset counters");
     cudaError_t e = kp::launch_user_pass(h->P, h->S, lambda, kp::MODE_HIST, 0, x_bits, st);
+    if (e == cudaErrorInvalidConfiguration)
+        return fail(KP_EINVAL, "kp_scd_breakpoints: the per-knapsack state of the breakpoint pass (K = %d) "
+                               "does not fit in shared memory", h->P.K);
     if (e != cudaSuccess) return cuda_fail(e, "user pass (breakpoints)");
     e = kp::launch_finalize(h->P, h->S, lambda, R, dual_sum, primal_sum, nullptr, 0.0, nullptr, st);
     if (e != cudaSuccess) return cuda_fail(e, "finalize");

@@ -32,7 +32,7 @@ constexpr int DENSE_TILE_BYTES = 64 * 1024;   // dense b tile
 constexpr int CSR_SETS = 2;                    // CSR user tiles per sweep phase (regular rows)
 
 struct SmemLayout {
-    size_t lamf, kinfo, ckey, wwin, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, total;
+    size_t lamf, kinfo, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -45,18 +45,15 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     o = align16(o + 4 * (size_t)K);
     s.kinfo = o;
     o = align16(o + 16 * (size_t)K);
-    s.ckey = o;
-    o = align16(o + 4 * (size_t)K);
-    s.wwin = o;
-    o = align16(o + 4 * (size_t)K);
     s.bcnt = o;
     o = align16(o + 4 * (size_t)K);
+    // refine ranges: re-run passes only
     s.lo = o;
-    o = align16(o + 4 * (size_t)K);
+    if (mode == MODE_REFINE) o = align16(o + 4 * (size_t)K);
     s.hi = o;
-    o = align16(o + 4 * (size_t)K);
+    if (mode == MODE_REFINE) o = align16(o + 4 * (size_t)K);
     s.shift = o;
-    o = align16(o + 4 * (size_t)K);
+    if (mode == MODE_REFINE) o = align16(o + 4 * (size_t)K);
     s.rfix = o;
     o = align16(o + 8 * (size_t)K);
     s.reg3 = o;
@@ -64,9 +61,9 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     s.red = o;
     o = align16(o + 2 * 8 * 32);
     if (layout == KP_B_CSR) {
-        s.rows = o;  // per thread: p~ row and rank masks (for shared-knapsack sweeps), margin row
+        s.rows = o;  // per thread: p~ row and rank masks (for shared-knapsack sweeps)
         // (rows of the register path only: M <= 16; `sets` sets of them)
-        if (mode != MODE_STATE && maxm <= 16) o = align16(o + (size_t)sets * 3 * 4 * (size_t)threads * maxm);
+        if (mode != MODE_STATE && maxm <= 16) o = align16(o + (size_t)sets * 2 * 4 * (size_t)threads * maxm);
         s.tile_p = s.tile_b = s.selm = o;
     } else {
         s.tile_p = o;
@@ -90,8 +87,6 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
                                                  unsigned char *smem, int round, bool leader) {
     const int K = P.K;
     float *lamf = (float *)(smem + L.lamf);
-    uint32_t *ckey = (uint32_t *)(smem + L.ckey);
-    int32_t *wwin = (int32_t *)(smem + L.wwin);
     uint32_t *bcnt = (uint32_t *)(smem + L.bcnt);
     uint32_t *lo = (uint32_t *)(smem + L.lo);
     uint32_t *hi = (uint32_t *)(smem + L.hi);
@@ -114,8 +109,6 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
             const long long wl = (long long)c - H, wh = (long long)c + H + 1;
             const uint32_t wlo = wl < 1 ? 1u : (uint32_t)wl;
             const uint32_t whi = wh > (long long)KEY_INF ? KEY_INF : (uint32_t)wh;
-            ckey[k] = c;
-            wwin[k] = sk.w;
             if (leader) {
                 S.sel[k].ckey = c;
                 S.sel[k].wlo = wlo;
@@ -221,6 +214,16 @@ __device__ __forceinline__ RefineSink make_refine_sink(const Params &P, const Sc
     rs.blk = blockIdx.x - S.g_lo;
     rs.bscale = P.bscale;
     return rs;
+}
+
+// a[j] for a run-time j without indexing a register array (which would move it
+// to local memory): a chain of selects
+template <int N>
+__device__ __forceinline__ float pick(const float (&a)[N], int j) {
+    float r = a[0];
+#pragma unroll
+    for (int q = 1; q < N; ++q) r = j == q ? a[q] : r;
+    return r;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -586,13 +589,9 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 tn[j] = dy[j] == l ? mn : tn[j];
             }
         }
-        float *mrow = prow + (size_t)blockDim.x * MAXM;  // this thread's margin row
         float mg[MAXM];
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j) {
-            mg[j] = pt[j] - (((G >> j) & 1u) ? ts[j] : tn[j]);
-            mrow[j] = mg[j];
-        }
+        for (int j = 0; j < MAXM; ++j) mg[j] = pt[j] - (((G >> j) & 1u) ? ts[j] : tn[j]);
         const uint2 shm = S.shmask[i];
         const uint32_t pending = shm.y;
         shared_entries = shm.x;
@@ -625,7 +624,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 inside &= inside - 1;
                 const int k = kid[e];
                 const float v = __ldg(val + e);
-                sink.buffer_add(k, breakpoint_value(kinfo[k].x, mrow[e / C], v), v);
+                sink.buffer_add(k, breakpoint_value(kinfo[k].x, pick(mg, e / C), v), v);
             }
         } else {
             // Algorithm 4 Map: closed form for knapsacks only one item touches.
@@ -634,7 +633,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
             int e = 0;
 #pragma unroll 1
             for (int j = 0; j < M; ++j) {
-                const float m = mg[j];
+                const float m = pick(mg, j);
                 const int c = C > 0 ? C : (int)nzr[j];
 #pragma unroll 1
                 for (int q = 0; q < c; ++q, ++e) {
@@ -649,7 +648,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
             }
         }
         if (pending) {
-            uint32_t *brow = reinterpret_cast<uint32_t *>(prow + 2 * (size_t)blockDim.x * MAXM);
+            uint32_t *brow = reinterpret_cast<uint32_t *>(prow + (size_t)blockDim.x * MAXM);
 #pragma unroll
             for (int j = 0; j < MAXM; ++j) {
                 prow[j] = pt[j];
@@ -714,16 +713,18 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
 // same time, so the sweep code and the per-user code do not compete for the
 // instruction cache.  Called by every thread of the block; contains the block
 // barriers that make the owners' rows visible and protect them until done.
+// Owner o = u * THREADS + thread is user base + o; with regular rows (C > 0)
+// its entries start at uoff0 + (base + o) * M * C, otherwise they are kept.
 template <int MAXM, int C, int THREADS, int U, class Sink>
 __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinfo, float *rows,
-                                             const int64_t (&ii)[U], const int64_t (&ee)[U],
+                                             int64_t base_user, const int64_t (&ee)[U],
                                              const uint32_t (&pend)[U], Sink &sink) {
     constexpr int QCAP = 2 * U * THREADS;
     constexpr int NW = THREADS / 32;
-    constexpr size_t SET = 3 * (size_t)THREADS * MAXM;  // rows of one user set
+    constexpr size_t SET = 2 * (size_t)THREADS * MAXM;  // rows of one user set
     static_assert(U * THREADS <= 16384, "task records hold the owner in 14 bits");
     __shared__ uint16_t q[QCAP];
-    __shared__ long long wi[U * THREADS], we0[U * THREADS];
+    __shared__ long long we0[C > 0 ? 1 : U * THREADS];
     __shared__ uint32_t wpy[U * THREADS];
     __shared__ int wtot[NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -732,8 +733,7 @@ __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinf
     for (int u = 0; u < U; ++u) {
         n += pair_count(pend[u]);
         if (pend[u]) {
-            wi[u * THREADS + threadIdx.x] = ii[u];
-            we0[u * THREADS + threadIdx.x] = ee[u];
+            if constexpr (C == 0) we0[u * THREADS + threadIdx.x] = ee[u];
             wpy[u * THREADS + threadIdx.x] = pend[u];
         }
     }
@@ -767,10 +767,11 @@ __device__ __forceinline__ void block_sweeps(const Params &P, const float4 *kinf
             const int owner = (int)(d >> 2), pt = (int)(d & 3u);
             const int ou = owner / THREADS, ot = owner - ou * THREADS;
             const float *prow = rows + ou * SET + (size_t)ot * MAXM;
-            const uint32_t *brow = reinterpret_cast<const uint32_t *>(prow + 2 * (size_t)THREADS * MAXM);
+            const uint32_t *brow = reinterpret_cast<const uint32_t *>(prow + (size_t)THREADS * MAXM);
             const uint32_t py = wpy[owner];
-            sweep_task<MAXM, C>(P, kinfo, prow, brow, wi[owner], we0[owner], pair_first(py, pt),
-                                pair_second(py, pt), sink);
+            const int64_t oi = base_user + owner;
+            const int64_t oe0 = C > 0 ? P.uoff0 + oi * (int64_t)(P.M * C) : we0[C > 0 ? 0 : owner];
+            sweep_task<MAXM, C>(P, kinfo, prow, brow, oi, oe0, pair_first(py, pt), pair_second(py, pt), sink);
         }
         __syncthreads();
     }
@@ -792,10 +793,10 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
         // the block meets its barriers once per CSR_SETS tiles (when the rows of
         // CSR_SETS tiles fit in shared memory next to the per-knapsack state)
         constexpr int U = CSR_SETS;
-        constexpr size_t SET = 3 * (size_t)THREADS * MAXM;
+        constexpr size_t SET = 2 * (size_t)THREADS * MAXM;
         const int64_t step = (int64_t)gridDim.x * THREADS * U;
         for (int64_t base = (int64_t)blockIdx.x * THREADS * U; base < P.N; base += step) {
-            int64_t ii[U], ee[U];
+            int64_t ee[U];
             uint32_t pend[U];
 #pragma unroll 1
             for (int u = 0; u < U; ++u) {
@@ -808,12 +809,11 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
 #pragma unroll
                 for (int v = 0; v < U; ++v)
                     if (v == u) {
-                        ii[v] = i;
                         ee[v] = e0;
                         pend[v] = pd;
                     }
             }
-            block_sweeps<MAXM, C, THREADS, U>(P, kinfo, rows, ii, ee, pend, sink);
+            block_sweeps<MAXM, C, THREADS, U>(P, kinfo, rows, base, ee, pend, sink);
         }
         return;
     }
@@ -851,9 +851,9 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
             }
         }
         if constexpr (MODE != MODE_STATE && MAXM <= 16) {
-            const int64_t ii[1] = {i}, ee[1] = {e0};
+            const int64_t ee[1] = {e0};
             const uint32_t pend[1] = {pending};
-            block_sweeps<MAXM, C, THREADS, 1>(P, kinfo, rows, ii, ee, pend, sink);
+            block_sweeps<MAXM, C, THREADS, 1>(P, kinfo, rows, base, ee, pend, sink);
         }
         if constexpr (C == 0) __syncthreads();
     }

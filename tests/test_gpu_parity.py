@@ -178,6 +178,41 @@ def test_scd_step_parity_wide_users(layout):
         assert np.all(lam_close(got, want)), (M, got, want)
 
 
+def test_scd_step_parity_largest_K():
+    """K = KP_MAX_K = 2048 on regular CSR rows (M = 10, 2 entries per item): the
+    per-knapsack state of the breakpoint pass is at its largest, the pass keeps one
+    user tile per sweep phase; the state and one SCD step against the oracle.  With
+    about 4 breakpoints per knapsack thresholds spread widely, down to 1e-5 of
+    lambda_k^t, where a FP32 breakpoint has lost relative precision: its absolute
+    error is a few ulps of s_j / b_jk (s_j = p_j + sum_k lambda_k b_jk, the scale
+    of the reduced cost), which is the floor allowed on top of 1e-5 relative."""
+    rng = np.random.default_rng(41)
+    M, K = 10, 2048
+    S, C = random_laminar(M, rng, max_nodes=4)
+    inst = gen.regular_csr(400, M, K, 2, seed=41, device="cuda", frac=0.2)
+    inst.S, inst.C = S, C
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    B = inst.B.cpu().numpy()
+    lam, _, _ = oracle.scd_step(p, b, S, C, rng.uniform(0, 0.8, size=K), B)
+    x, R, d, pr, g, _ = cuda_state(prob, torch.tensor(lam, device="cuda"))
+    xo, Ro, do, po = oracle.user_pass(p, b, S, C, lam)
+    compare_state(p, b, lam, x, R, d, pr, xo, Ro, do, po)
+    got, Rb, db, pb = _scd_gpu_state(prob, lam)
+    _check_breakpoint_state(p, b, lam, Rb, db, pb, Ro, do, po)
+    want, _, _ = oracle.scd_step(p, b, S, C, lam, B)
+    # with about 4 breakpoints per knapsack one user whose reduced costs are
+    # near-tied (decisions excused above) can move a threshold to its neighbour:
+    # every knapsack that differs must be touched by such a user
+    s_over_b = np.where(b > 0, (p + np.einsum("ijk,k->ij", b, lam))[:, :, None] / np.where(b > 0, b, 1), 0)
+    floor = 4 * 2.0 ** -24 * s_over_b.max(axis=(0, 1))
+    bad = np.nonzero(np.abs(got - want) > REL_LAMBDA * np.abs(want) + floor)[0]
+    exc = excused_users(p, b, lam)
+    touched = (b[exc] > 0).any(axis=(0, 1)) if exc.any() else np.zeros(K, dtype=bool)
+    assert np.all(touched[bad]), (bad[~touched[bad]], got[bad], want[bad])
+    assert len(bad) <= 0.01 * K, len(bad)
+
+
 def test_scd_trajectory_small_config():
     """N=1e4, M=10, K=5: 50 SCD iterations; each GPU step matches the oracle's step
     taken at the GPU's own lambda^t."""
