@@ -29,7 +29,7 @@ namespace kp {
 namespace {
 
 constexpr int DENSE_TILE_BYTES = 64 * 1024;   // dense b tile
-constexpr int CSR_SETS = 2;                    // CSR user tiles per sweep phase (regular rows)
+constexpr int CSR_SETS = 3;                    // CSR user tiles per sweep phase (regular rows)
 
 struct SmemLayout {
     size_t lamf, kinfo, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, total;
