@@ -75,6 +75,18 @@ def algo_bytes_per_user(inst):
     return 4 * inst.M + 4 * inst.M * inst.K
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over the ranks of the job (replicas: the job's time is
+    its slowest rank's); x itself when there is one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
@@ -367,10 +379,7 @@ def main():
         dist.barrier()
     kp.kp_device_status(prob)
     ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t)
+    ms_total = max_over_ranks(ms_total, world, dev)
     pass_ms = [a.elapsed_time(b) for a, b in ev]
     value = N * args.steps * world / (ms_total / 1e3)
 
