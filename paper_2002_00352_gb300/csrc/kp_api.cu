@@ -271,7 +271,9 @@ kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget
                 int dev = 0, sms = 1;
                 cudaGetDevice(&dev);
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-                const long long want = (S.nrare + 255) / 256;
+                // two resident blocks of 512 threads per SM (each owns buffer slots,
+                // so few large blocks rather than many small ones)
+                const long long want = (S.nrare + 511) / 512;
                 rare_grid = (int)(want < 2 * sms ? want : 2 * sms);
             }
         }

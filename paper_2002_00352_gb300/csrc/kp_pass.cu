@@ -889,7 +889,7 @@ __global__ void __launch_bounds__(THREADS, 1) csr_pass_kernel(Params P, Scratch 
 // moving lines).  Keeping them out of the user pass keeps its sweep phase
 // uniform across the lanes.  The blocks own buffer blocks
 // [rare_blk0, rare_blk0 + rare_grid).
-constexpr int RARE_THREADS = 256;
+constexpr int RARE_THREADS = 512;
 constexpr int XMAX = 3;
 
 template <int MAXM, int C, class Sink>
@@ -981,7 +981,7 @@ __device__ __forceinline__ void rare_task(const Params &P, const float4 *kinfo, 
 }
 
 template <int MAXM, int C, int MODE>
-__global__ void __launch_bounds__(RARE_THREADS) rare_kernel(Params P, Scratch S, const double *lam, int round) {
+__global__ void __launch_bounds__(RARE_THREADS, 2) rare_kernel(Params P, Scratch S, const double *lam, int round) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
     const SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, 1, RARE_THREADS, 0, MODE);
