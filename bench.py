@@ -448,8 +448,11 @@ def main():
         e_ms = e0.elapsed_time(e1)
         result["e2e"] = {"value": N * args.steps / (e_ms / 1e3), "unit": UNIT,
                          "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 2 * K * 8,
-                         "note": "instance copied host->device once per job of `steps` iterations; "
-                                 "lambda and R read back at the end"}
+                         "note": "a job of `steps` SCD iterations from lambda = 0 through the C ABI: "
+                                 "instance copied host->device (pinned) once per job, lambda and R "
+                                 "read back at the end; unlike `value` it includes the first "
+                                 "iterations, whose thresholds lie far from any prediction and "
+                                 "take re-run passes"}
     if not args.no_cpu and rank == 0:
         try:
             result["cpu_baseline"] = cpu_baseline(inst, min(args.cpu_sample, N))
