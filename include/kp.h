@@ -136,18 +136,24 @@ kp_status kp_dual_value(kp_problem *h, const double *lambda, double *g, void *st
 kp_status kp_dd_step(kp_problem *h, const double *lambda, double alpha, double *lambda_next,
                      double *R, void *stream);
 
-/* Map of Algorithm 4 (with the candidate sets of Algorithm 3) at lambda:
- * every user's breakpoints of its k-consumption in lambda_k (others fixed)
- * are aggregated into the handle's per-knapsack histograms (Sec. 5.2's
- * bucketing, centred at lambda_k).  The state at lambda is reduced in the
- * same pass into the optional outputs (as in kp_reduce_consumption).
- * Must be followed by kp_threshold_select with the same lambda. */
+/* Map of Algorithm 4 (the step functions that Algorithm 3's candidates
+ * describe) at lambda: every user's breakpoints of its k-consumption in
+ * lambda_k (others fixed) are aggregated into the handle's per-knapsack
+ * masses around a predicted threshold (Sec. 5.2 centres its buckets at
+ * lambda_k), the ones close to it buffered.  The state at lambda is reduced
+ * in the same pass into the optional outputs (as in kp_reduce_consumption);
+ * for CSR rows with the same number of entries per item, R is the mass of
+ * the breakpoints above lambda_k, which equals the consumption up to users
+ * whose reduced costs tie within FP32 rounding.  Must be followed by
+ * kp_threshold_select with the same lambda.  KP_EINVAL when the per-knapsack
+ * state does not fit in shared memory (K near KP_MAX_K with more than 10
+ * items per user). */
 kp_status kp_scd_breakpoints(kp_problem *h, const double *lambda, double *R, double *dual_sum,
                              double *primal_sum, uint32_t *x_bits, void *stream);
 
 /* Reduce of Algorithm 4 for every k:
  *   lambda_next_k = min { v in {0} U {breakpoints} : sum_{v1 > v} v2 <= B_k }
- * found exactly among the FP32 breakpoints (histogram, then a buffered
+ * found exactly among the FP32 breakpoints (window masses, then a buffered
  * exact selection; when the crossing lies outside the buffered window the
  * user pass is re-run to narrow it, up to a fixed number of rounds, all on
  * the device).  lambda must be the one given to kp_scd_breakpoints.

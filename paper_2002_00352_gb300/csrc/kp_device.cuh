@@ -17,7 +17,13 @@
 //                 consumption can only change where a line crosses zero or two
 //                 adjacent lines swap, and at such an event only the two items
 //                 involved can change membership.  Every increase is emitted as
-//                 (v1 = lambda_k at the event, v2 = increase).
+//                 (v1 = lambda_k at the event, v2 = increase).  Used for dense
+//                 rows and long CSR rows.
+//  exchange_sweep the same map in exchange form (only the events that change
+//                 the selection, found from circuit minima), for a few moving
+//                 lines; pair_sweep: its straight-line form for two.
+//  WindowSink, RefineSink  where the breakpoints go (window masses and
+//                 buffer; sub-histogram of a re-run range).
 #pragma once
 #include <cfloat>
 #include <cstdint>

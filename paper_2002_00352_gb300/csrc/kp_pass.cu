@@ -10,15 +10,18 @@
 //                its k-consumption, aggregated per knapsack into the exact
 //                masses above / inside / below a window around the predicted
 //                threshold (Sec. 5.2 centres its buckets at lambda_k^t), with
-//                the breakpoints inside the window buffered.
+//                the breakpoints inside the window buffered.  A knapsack one
+//                item of the user touches has a closed-form breakpoint; two
+//                items: pair_sweep in a block-wide sweep phase; three or more:
+//                rare_kernel (a launch of its own).
 //   MODE_REFINE  Algorithm 4's Map restricted to the key ranges still
 //                unresolved by the threshold selection.
 //
 // Reductions: FP32 per user, exact 64-bit fixed point per knapsack (integer
 // atomics, so the result does not depend on the order of the additions),
-// FP64 per block for the objective sums and an ordered sum over blocks in
-// the finalize kernel.  The grid is persistent and users are assigned to
-// blocks statically, so every sum is reproducible run to run.
+// 64-bit fixed point for the objective sums too.  The grid is persistent and
+// users are assigned to blocks statically, so every sum is reproducible run
+// to run.
 #include <cstdio>
 
 #include "kp_device.cuh"
@@ -535,14 +538,14 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
         float du = 0.f, pu = 0.f;
         if constexpr (C > 0) {
 #pragma unroll
-            for (int j = 0; j < MAXM; ++j)
-                if ((G >> j) & 1u) {
-                    du += pt[j];
-                    pu += __ldg(pr + j);
-                    if (!FOLD)
+            for (int j = 0; j < MAXM; ++j) {
+                const uint32_t sj = (G >> j) & 1u;
+                du += sj ? pt[j] : 0.f;
+                pu += sj ? __ldg(pr + j) : 0.f;
+                if (!FOLD)
 #pragma unroll
-                        for (int q = 0; q < C; ++q) shared_add_u64(&rfix[kk[j * C + q]], bmass(vv[j * C + q], P.bscale));
-                }
+                    for (int q = 0; q < C; ++q) shared_add_u64_if(&rfix[kk[j * C + q]], bmass(vv[j * C + q], P.bscale), sj);
+            }
         } else {
             int e = 0;
 #pragma unroll
