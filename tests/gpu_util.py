@@ -52,6 +52,19 @@ def lam_close(a, b, rel=REL_LAMBDA, abs_floor=1e-12):
     return np.abs(a - b) <= rel * np.maximum(np.abs(b), np.abs(a)) + abs_floor
 
 
+def lam_close_fp32(got, want, p, b, lam_t, rel=REL_LAMBDA):
+    """lam_close with the floor of a FP32 breakpoint lambda_k^t + m / b_jk: its
+    absolute error is a few ulps of s_j / b_jk (s_j = p_j + sum_k lambda_k b_jk,
+    the scale of the reduced cost), which shows when a threshold lands far
+    below lambda_k^t or the other quantities of its users."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    s = p + np.einsum("ijk,k->ij", b, lam_t)
+    s_over_b = np.where(b > 0, s[:, :, None] / np.where(b > 0, b, 1.0), 0.0)
+    floor = 4 * 2.0 ** -24 * s_over_b.max(axis=(0, 1))
+    return np.abs(got - want) <= rel * np.maximum(np.abs(got), np.abs(want)) + floor + 1e-12
+
+
 def cuda_state(prob, lam_t):
     from paper_2002_00352_gb300 import kp
     K = prob.K
