@@ -23,6 +23,12 @@ namespace {
 
 __device__ __forceinline__ int bitlen32(uint32_t x) { return x ? 32 - __clz(x) : 0; }
 
+// Largest half-width of the window, in keys (2^21 keys: about +-25 % in value).
+// After a large move of lambda_k a window as wide as the miss holds more
+// breakpoints than the buffer keeps, which costs re-run passes just as a miss
+// does; on the 1e8-user workload the cap saves three passes of the first steps.
+constexpr int WMAX_BITS = 21;
+
 __device__ __forceinline__ unsigned long long budget_fixed(double Bk, int fixs) {
     double v = ldexp(Bk, fixs);
     if (!(v > 0.0)) return 0ull;
@@ -161,7 +167,7 @@ __device__ __forceinline__ void resolved(SelK &sk, int k, uint32_t key, float la
     if (key) {
         const uint32_t err = key > sk.ckey ? key - sk.ckey : sk.ckey - key;
         const int w = bitlen32(err) + 1;
-        sk.w = w < WMIN_BITS ? WMIN_BITS : (w > 30 ? 30 : w);
+        sk.w = w < WMIN_BITS ? WMIN_BITS : (w > WMAX_BITS ? WMAX_BITS : w);
         sk.last_nz_key = key;
     }
     sk.prev_key = cur;
