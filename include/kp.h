@@ -251,6 +251,17 @@ kp_status kp_device_status(kp_problem *h, void *stream);
  * from the histogram alone (lambda = 0), out[2] = buffer overflows. */
 kp_status kp_select_stats(kp_problem *h, int64_t out[3], void *stream);
 
+/* Pre-solving by sampling (Sec. 5.3): iters iterations of Algorithm 4 from
+ * lambda = 0 on the users users[0..n) (device int64 [n], each in 0..N-1,
+ * drawn by the caller, e.g. uniformly without replacement) with every budget
+ * scaled by n / N; the result, a starting point for the whole instance, is
+ * written to lambda0 (device float64 [K]).  The sample's rows are gathered
+ * into buffers of its own and a handle is created over them for the call
+ * (allocates; synchronous).  KP_EINVAL for a bad argument or an index
+ * outside 0..N-1. */
+kp_status kp_presolve(kp_problem *h, const int64_t *users, int64_t n, int32_t iters, double *lambda0,
+                      void *stream);
+
 /* Launch layout of a handle (host values, no device work): out[0] = blocks of
  * the user pass, out[1] = users whose knapsacks shared by three or more of
  * their items are swept by a separate kernel (CSR; each breakpoint pass then

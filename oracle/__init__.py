@@ -201,6 +201,21 @@ def scd_step(p, b, S, C, lam, B):
     return out, nemit, mass
 
 
+def presolve(p, b, S, C, B, users, iters):
+    """Sec. 5.3 pre-solving by sampling: `iters` steps of Algorithm 4 from lambda = 0
+    on the users `users` with every budget scaled by n / N (composition of the
+    routines above)."""
+    users = np.asarray(users, dtype=np.int64)
+    p, b = _f64(p), _f64(b)
+    N = p.shape[0]
+    ps, bs = p[users], b[users]
+    Bs = _f64(B) * (len(users) / N)
+    lam = np.zeros(b.shape[2])
+    for _ in range(int(iters)):
+        lam, _, _ = scd_step(ps, bs, S, C, lam, Bs)
+    return lam
+
+
 def postprocess(p, b, lam, B, x):
     """Sec. 5.4: returns (feasible x, number of users reset)."""
     p, b, lam, B = _f64(p), _f64(b), _f64(lam), _f64(B)

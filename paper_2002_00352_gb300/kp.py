@@ -52,7 +52,8 @@ class kp_desc(ctypes.Structure):
 EXPORTS = [
     "kp_create", "kp_destroy", "kp_solve_users", "kp_reduce_consumption", "kp_dual_value",
     "kp_dd_step", "kp_scd_breakpoints", "kp_threshold_select", "kp_scd_step",
-    "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_info", "kp_last_error", "kp_version",
+    "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_info", "kp_presolve", "kp_last_error",
+    "kp_version",
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
     "kp_autotune",
@@ -79,6 +80,7 @@ def load_library(path: Optional[str] = None):
     lib.kp_device_status.argtypes = [P, P]
     lib.kp_select_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
     lib.kp_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+    lib.kp_presolve.argtypes = [P, P, i64, i32, P, P]
     lib.kp_reduce_consumption_noalloc.argtypes = [ctypes.POINTER(kp_desc), P, P, P, P, P, P, P]
     lib.kp_batch_create.argtypes = [ctypes.POINTER(kp_desc), i32, ctypes.POINTER(ctypes.c_void_p)]
     lib.kp_batch_destroy.argtypes = [P]
@@ -287,6 +289,17 @@ def kp_select_stats(prob: Problem, stream=None):
     out = (ctypes.c_int64 * 3)()
     _check(load_library().kp_select_stats(prob.handle, out, _stream(stream)))
     return list(out)
+
+
+def kp_presolve(prob: Problem, users, iters: int, lambda0=None, stream=None):
+    """Sec. 5.3: SCD on the sampled users (device int64 tensor) with budgets scaled by
+    n / N; returns (or fills) lambda0, a float64 device tensor of K entries."""
+    if lambda0 is None:
+        lambda0 = torch.empty(prob.K, dtype=torch.float64, device="cuda")
+    users = users.contiguous()
+    _check(load_library().kp_presolve(prob.handle, _ptr(users, torch.int64, "users"), users.numel(),
+                                      int(iters), _ptr(lambda0, torch.float64, "lambda0"), _stream(stream)))
+    return lambda0
 
 
 def kp_info(prob: Problem) -> dict:

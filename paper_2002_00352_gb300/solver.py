@@ -57,6 +57,15 @@ def dd_solve(prob, lam0: torch.Tensor, alpha: float, iters: int, record: bool = 
     return a, hist
 
 
+def presolve(prob, n: int, iters: int, seed: int = 0) -> torch.Tensor:
+    """Sec. 5.3: lambda^0 from `iters` SCD iterations on about n users drawn
+    uniformly (seeded; n draws, repeats dropped), budgets scaled by the sample's
+    share of the users (kp_presolve)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    users = torch.unique(torch.randint(0, prob.N, (min(n, prob.N),), generator=g)).to("cuda")
+    return kp.kp_presolve(prob, users, iters)
+
+
 class ScdGraph:
     """Two SCD iterations (lambda_a -> lambda_b -> lambda_a) captured in one CUDA
     graph; replay() advances the state by two iterations with one launch."""

@@ -212,6 +212,27 @@ def test_scd_step_parity_largest_K():
     assert len(bad) <= 0.01 * K, len(bad)
 
 
+@pytest.mark.parametrize("which", ["dense", "csr"])
+def test_presolve_matches_oracle(which):
+    """Sec. 5.3: kp_presolve on a sampled quarter of the users (budgets scaled by
+    n / N) against the oracle's SCD on the same sample: one step (1e-5 relative)
+    and three steps (each step's small differences may move the next threshold
+    to a neighbouring breakpoint: 1e-4 relative)."""
+    inst = gen.small_dd_scd(device="cuda") if which == "dense" else gen.sparse_csr(N=20_000, device="cuda")
+    prob = _problem(inst)
+    p, b = _dense_np(inst)
+    B = inst.B.cpu().numpy()
+    g = torch.Generator(device="cpu").manual_seed(11)
+    users = torch.randperm(inst.N, generator=g)[: inst.N // 4].sort().values
+    for iters, rel in ((1, REL_LAMBDA), (3, 1e-4)):
+        got = kp.kp_presolve(prob, users.to("cuda"), iters).cpu().numpy()
+        want = oracle.presolve(p, b, inst.S, inst.C, B, users.numpy(), iters)
+        ok = lam_close_fp32(got, want, p[users.numpy()], b[users.numpy()], want, rel=rel)
+        assert ok.all(), (iters, got[~ok], want[~ok])
+    with pytest.raises(kp.KpError):
+        kp.kp_presolve(prob, torch.tensor([0, inst.N], dtype=torch.int64, device="cuda"), 1)
+
+
 def test_scd_trajectory_small_config():
     """N=1e4, M=10, K=5: 50 SCD iterations; each GPU step matches the oracle's step
     taken at the GPU's own lambda^t."""

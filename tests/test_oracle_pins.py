@@ -397,3 +397,25 @@ def test_scd_emitted_mass_is_consumption_at_zero():
         lam0[k] = 1e-12
         _, R0, _, _ = oracle.user_pass(p, b, S, C, lam0)
         assert mass[k] == pytest.approx(R0[k], rel=1e-12)
+
+
+def test_presolve_scaling_on_a_doubled_instance():
+    """Sec. 5.3: sampling the first copy of an instance whose users all appear twice
+    (budgets = those of the doubled instance) scales the budgets back to the
+    original's, so pre-solving equals plain SCD on the original instance."""
+    rng = np.random.default_rng(3)
+    N, M, K = 40, 4, 2
+    p = rng.uniform(0, 1, (N, M))
+    b = rng.uniform(0, 1, (N, M, K))
+    S, C = [0b1111], [2]
+    B = 0.3 * b.sum(axis=(0, 1))
+    p2, b2 = np.concatenate([p, p]), np.concatenate([b, b])
+    B2 = 2 * B
+    lam = np.zeros(K)
+    for _ in range(3):
+        lam, _, _ = oracle.scd_step(p, b, S, C, lam, B)
+    got = oracle.presolve(p2, b2, S, C, B2, np.arange(N), 3)
+    assert np.allclose(got, lam, rtol=0, atol=0)
+    # the whole instance as the sample: plain SCD on it
+    full = oracle.presolve(p, b, S, C, B, np.arange(N), 3)
+    assert np.allclose(full, lam, rtol=0, atol=0)
