@@ -88,11 +88,18 @@ def max_over_ranks(x: float, world: int, device) -> float:
 
 
 def kernel_source_hash():
+    """Hash of the breakpoint pass's sources with comments and blank lines removed
+    (a capture stays valid across comment edits, not across code changes)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ["kp_pass.cu", "kp_device.cuh", "kp_internal.h"]:
-        with open(os.path.join(ROOT, "paper_2002_00352_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2002_00352_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

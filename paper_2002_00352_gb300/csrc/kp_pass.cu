@@ -235,8 +235,9 @@ __device__ __forceinline__ float pick(const float (&a)[N], int j) {
 // of the users' entry counts (csr_user_off is consistent with csr_item_nnz,
 // checked at creation).  Entries whose knapsack is also consumed by another
 // item of the same user are marked once at creation (Scratch::shmask); all
-// other entries get the closed-form breakpoint in one uniform loop, and the
-// few shared knapsacks run the kinetic sweep afterwards.
+// other entries get the closed-form breakpoint in one uniform loop; knapsacks
+// two items share get a pair sweep in the block's sweep phase, those three or
+// more share are left to rare_kernel.
 // ------------------------------------------------------------------------------------------
 template <int THREADS>
 __device__ __forceinline__ int block_excl_scan(int v, int *s_scan) {
@@ -408,9 +409,9 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
 //   Algorithm 1 is evaluated in its literal bottom-up form: beats[j] is the set
 //   of items ranked before j (larger p~, ties to the lower index); at set S_l
 //   an item survives if fewer than C_l survivors of S_l rank before it.
-// Returns the entries whose knapsack another item of the user also uses and
-// that are the first of their knapsack (they need the kinetic sweep); the
-// user's p~ row is then left in prow.
+// Returns the user's list of knapsacks that exactly two of its items use
+// (shmask.y: they need a pair sweep); the user's p~ row and rank masks are
+// then left in prow (and the row after it).
 template <int MAXM, int C, int MODE, class Sink>
 __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch &S, int64_t i,
                                                   int64_t e0, const float *lamf, const float4 *kinfo,
