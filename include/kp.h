@@ -262,6 +262,27 @@ kp_status kp_select_stats(kp_problem *h, int64_t out[3], void *stream);
 kp_status kp_presolve(kp_problem *h, const int64_t *users, int64_t n, int32_t iters, double *lambda0,
                       void *stream);
 
+/* Post-processing for feasibility (Sec. 5.4).  Users are taken in
+ * non-decreasing order of their cost-adjusted group profit
+ *     q_i = sum_{j : x_ij = 1} (p_ij - sum_k lambda_k b_ijk)
+ * (q_i in FP64, items in ascending j and each item's knapsacks in ascending
+ * k, every product and sum rounded to nearest; equal q_i: lower i first), and
+ * every decision of a user is reset, in that order, until no knapsack exceeds
+ * its budget (the users reset form the shortest such prefix; none if x is
+ * already feasible).
+ *   lambda   device float64 [K]: the multipliers that define q_i
+ *   x_bits   device uint32 [N*W] as in kp_solve_users, any decisions; the
+ *            reset users' words are zeroed in place, the others untouched
+ *   reset    device int64 scalar: number of users reset (nullable)
+ *   R_after  device float64 [K]: consumption of the returned x, summed in
+ *            the fixed point of kp_reduce_consumption (nullable)
+ * Budgets are compared in that fixed point (units of 2^-s with every entry's
+ * b below 2^30 units).  Asynchronous on the stream; takes 8 N + O(K) bytes of
+ * stream-ordered device memory for the call.  An inconsistent selection (not
+ * expected) is reported as KP_ESTATE by kp_device_status. */
+kp_status kp_postprocess(kp_problem *h, const double *lambda, uint32_t *x_bits, int64_t *reset,
+                         double *R_after, void *stream);
+
 /* Launch layout of a handle (host values, no device work): out[0] = blocks of
  * the user pass, out[1] = users whose knapsacks shared by three or more of
  * their items are swept by a separate kernel (CSR; each breakpoint pass then

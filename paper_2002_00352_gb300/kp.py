@@ -52,7 +52,8 @@ class kp_desc(ctypes.Structure):
 EXPORTS = [
     "kp_create", "kp_destroy", "kp_solve_users", "kp_reduce_consumption", "kp_dual_value",
     "kp_dd_step", "kp_scd_breakpoints", "kp_threshold_select", "kp_scd_step",
-    "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_info", "kp_presolve", "kp_last_error",
+    "kp_dual_backward", "kp_device_status", "kp_select_stats", "kp_info", "kp_presolve", "kp_postprocess",
+    "kp_last_error",
     "kp_version",
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
@@ -81,6 +82,7 @@ def load_library(path: Optional[str] = None):
     lib.kp_select_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
     lib.kp_info.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
     lib.kp_presolve.argtypes = [P, P, i64, i32, P, P]
+    lib.kp_postprocess.argtypes = [P, P, P, P, P, P]
     lib.kp_reduce_consumption_noalloc.argtypes = [ctypes.POINTER(kp_desc), P, P, P, P, P, P, P]
     lib.kp_batch_create.argtypes = [ctypes.POINTER(kp_desc), i32, ctypes.POINTER(ctypes.c_void_p)]
     lib.kp_batch_destroy.argtypes = [P]
@@ -300,6 +302,20 @@ def kp_presolve(prob: Problem, users, iters: int, lambda0=None, stream=None):
     _check(load_library().kp_presolve(prob.handle, _ptr(users, torch.int64, "users"), users.numel(),
                                       int(iters), _ptr(lambda0, torch.float64, "lambda0"), _stream(stream)))
     return lambda0
+
+
+def kp_postprocess(prob: Problem, lam, x_bits, reset=None, R_after=None, stream=None):
+    """Sec. 5.4: resets users in order of their cost-adjusted group profit until x
+    (int32 words, modified in place) fits every budget.  Returns (reset, R_after):
+    a device int64 scalar tensor and a float64 [K] device tensor."""
+    if reset is None:
+        reset = torch.empty((), dtype=torch.int64, device="cuda")
+    if R_after is None:
+        R_after = torch.empty(prob.K, dtype=torch.float64, device="cuda")
+    _check(load_library().kp_postprocess(
+        prob.handle, _ptr(lam, torch.float64, "lambda"), _ptr(x_bits, None, "x_bits"),
+        _ptr(reset, torch.int64, "reset"), _ptr(R_after, torch.float64, "R_after"), _stream(stream)))
+    return reset, R_after
 
 
 def kp_info(prob: Problem) -> dict:
