@@ -132,15 +132,35 @@ def test_postprocess_equal_keys_lower_index_first():
     _check(p, b, lam, B, x, _gpu(prob, lam, x))
 
 
-def test_postprocess_many_knapsacks_three_bit_digits():
-    """K = 900: the per-digit masses take 3-bit digits (another level count)."""
+def test_postprocess_all_users_identical():
+    """Every key equal (no key bit separates the users): the order is the user
+    index alone."""
+    rng = np.random.default_rng(10)
+    N, M, K = 257, 3, 2
+    p = np.tile(rng.random((1, M)).astype(np.float32), (N, 1))
+    b = np.tile(rng.random((1, M, K)).astype(np.float32), (N, 1, 1))
+    x = np.tile(np.array([[1, 0, 1]], dtype=np.int32), (N, 1))
+    R = np.einsum("nmk,nm->k", b.astype(np.float64), x.astype(np.float64))
+    B = R * np.array([0.61, 0.93])
+    tp, tb = torch.tensor(p, device="cuda"), torch.tensor(b, device="cuda")
+    prob = kp.kp_create(N, M, K, tp.reshape(-1), torch.tensor(B, device="cuda"), [], [],
+                        b_dense=tb.reshape(-1))
+    lam = np.array([0.125, 0.5])
+    r = _check(p, b, lam, B, x, _gpu(prob, lam, x))
+    assert 0 < r < N
+
+
+@pytest.mark.parametrize("K,hi", [(900, 1.1), (2048, 0.9)])
+def test_postprocess_many_knapsacks_narrow_digits(K, hi):
+    """Many knapsacks over budget: the per-digit sums leave room for 4-bit
+    (K = 900, about 750 over budget) or 3-bit digits (K = 2048, all over)."""
     rng = np.random.default_rng(9)
-    N, M, K = 400, 3, 900
+    N, M = 300, 2
     inst = gen.random_small(N, M, K, seed=9, device="cuda", layout="dense")
     p, b = inst.to_dense_numpy()
     x = (rng.random((N, M)) < 0.6).astype(np.int32)
     R = np.einsum("nmk,nm->k", b, x.astype(np.float64))
-    B = _budgets(R, rng, 0.5, 1.1)
+    B = _budgets(R, rng, 0.5, hi)
     inst.B = torch.tensor(B, device="cuda")
     prob = kp.kp_create_from_instance(inst)
     lam = rng.uniform(0, 0.01, size=K)
