@@ -71,6 +71,22 @@ def test_postprocess_random_x(layout, seed):
     assert r > 0
 
 
+def test_postprocess_csr_wide_rows():
+    """CSR with M = 16 and up to 48 entries per user: some tiles of 256 users hold
+    more entries than the shared-memory stage and are read from global memory."""
+    rng = np.random.default_rng(4)
+    N, M, K = 3001, 16, 6
+    inst = gen.random_small(N, M, K, seed=4, device="cuda", layout="csr")
+    p, b = inst.to_dense_numpy()
+    x = (rng.random((N, M)) < 0.5).astype(np.int32)
+    R = np.einsum("nmk,nm->k", b, x.astype(np.float64))
+    B = _budgets(R, rng)
+    inst.B = torch.tensor(B, device="cuda")
+    prob = kp.kp_create_from_instance(inst)
+    lam = rng.uniform(0, 0.3, size=K)
+    assert _check(p, b, lam, B, x, _gpu(prob, lam, x)) > 0
+
+
 @pytest.mark.parametrize("layout", ["dense", "csr"])
 def test_postprocess_greedy_x(layout):
     """x = the oracle's Algorithm 1 decisions at lambda = 0 and at a small lambda
