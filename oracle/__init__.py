@@ -8,7 +8,8 @@ shares no code with that path.
 The arithmetic lives in ``kp_oracle.c`` (plain C, double precision, one
 routine per step of the paper: Sec. 4.2 and Algorithm 1 for the per-user
 greedy, Eq. (14) and Algorithm 2 for dual descent, Algorithms 3-4 for
-synchronous coordinate descent, Sec. 5.4 for post-processing).  This module
+synchronous coordinate descent, Algorithm 5 for its one-item-per-knapsack
+special case, Sec. 5.4 for post-processing).  This module
 only marshals numpy arrays into those routines and converts the CSR storage of
 ``b`` into the dense layout the oracle reads.
 """
@@ -65,6 +66,9 @@ def _load():
     lib.kpo_scd_step.restype = i64
     lib.kpo_postprocess.argtypes = [i64, i32, i32, P, P, P, P, P]
     lib.kpo_postprocess.restype = i64
+    lib.kpo_alg5_map_user.argtypes = [i32, P, P, i32, P, P, P, P, P]
+    lib.kpo_alg5_step.argtypes = [i64, i32, P, P, i32, P, P, P]
+    lib.kpo_alg5_step.restype = i64
     lib.kpo_num_threads.restype = i32
     _lib = lib
     return lib
@@ -223,6 +227,32 @@ def postprocess(p, b, lam, B, x):
     N, M, K = b.shape
     r = _load().kpo_postprocess(N, M, K, _ptr(p), _ptr(b), _ptr(lam), _ptr(B), _ptr(x))
     return x, int(r)
+
+
+def alg5_map_user(p_i, bdiag_i, Q, lam):
+    """Algorithm 5 (Sec. 5.1) for one user with M = K items, item k consuming only
+    knapsack k (b_ikk = bdiag_i[k]), at most Q items: arrays (k, v1, v2)."""
+    p_i, bdiag_i, lam = _f64(p_i), _f64(bdiag_i), _f64(lam)
+    K = p_i.shape[0]
+    ek = np.zeros(K, dtype=np.int32)
+    v1 = np.zeros(K)
+    v2 = np.zeros(K)
+    n = ctypes.c_int64(0)
+    _load().kpo_alg5_map_user(K, _ptr(p_i), _ptr(bdiag_i), int(Q), _ptr(lam), ctypes.byref(n),
+                              _ptr(ek), _ptr(v1), _ptr(v2))
+    m = n.value
+    return ek[:m].copy(), v1[:m].copy(), v2[:m].copy()
+
+
+def alg5_step(p, bdiag, Q, lam, B):
+    """One Algorithm 4 iteration with Algorithm 5 as Map (p, bdiag [N, K]): lam_next [K]."""
+    p, bdiag, lam, B = _f64(p), _f64(bdiag), _f64(lam), _f64(B)
+    N, K = p.shape
+    out = np.zeros(K)
+    r = _load().kpo_alg5_step(N, K, _ptr(p), _ptr(bdiag), int(Q), _ptr(lam), _ptr(B), _ptr(out))
+    if r < 0:
+        raise MemoryError("oracle alg5_step: allocation failed")
+    return out
 
 
 def densify_csr(N, M, K, user_off, item_nnz, val, kidx) -> np.ndarray:

@@ -31,6 +31,10 @@
  *   kpo_scd_step        one synchronous coordinate-descent iteration
  *                       (Algorithm 4's loop body).
  *   kpo_postprocess     Sec. 5.4, post-processing for feasibility.
+ *   kpo_alg5_map_user   Algorithm 5 (Sec. 5.1): the linear-time Map for one
+ *                       item per knapsack (M = K, b_ijk = 0 for j != k) and
+ *                       one cap Q on the number of items of a user.
+ *   kpo_alg5_step       one iteration of Algorithm 4 with Algorithm 5 as Map.
  *
  * Readings of passages that are ambiguous in the paper (each listed in the
  * design notes of the repository):
@@ -57,6 +61,10 @@
  *   R7  Post-processing zeroes users in non-decreasing order of the
  *       cost-adjusted group profit (ties: lower user index first), every
  *       user in that order, until all global constraints hold.
+ *   R12 Algorithm 5's n-th largest adjusted profit, for n larger than the
+ *       number of items K, is 0 (the adjusted profits are clamped at 0, so
+ *       missing ranks act as items of profit 0); an item with b_ikk = 0 has
+ *       no candidate (as R5 for parallel lines).
  *
  * Layout: p is [N][M], b is dense [N][M][K] with k fastest, lam and B are
  * [K]; local constraints are L item sets given as bitmasks S[l] over the M
@@ -566,6 +574,116 @@ int64_t kpo_postprocess(int64_t N, int M, int K, const double *p,
     free(R);
     free(u);
     return reset;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 5 (Sec. 5.1): Map of one user when item k is the only item that */
+/* consumes knapsack k (M = K) and one local constraint allows at most Q     */
+/* items.  pi[k] = p_ik, bi[k] = b_ikk.  Emits at most one (k, v1, v2) per k */
+/* into ek / ev1 / ev2; *n receives their number.                            */
+/* ------------------------------------------------------------------------ */
+static int cmp_double_desc(const void *x, const void *y)
+{
+    double a = *(const double *)x, b = *(const double *)y;
+    return (a < b) - (a > b);
+}
+
+/* n-th largest of the K adjusted profits (n >= 1); 0 beyond K (R12) */
+static double nth_largest(const double *sorted_desc, int K, int n)
+{
+    return n <= K ? sorted_desc[n - 1] : 0.0;
+}
+
+void kpo_alg5_map_user(int K, const double *pi, const double *bi, int Q,
+                       const double *lam, int64_t *n, int32_t *ek,
+                       double *ev1, double *ev2)
+{
+    double *adj = (double *)malloc(sizeof(double) * (size_t)K);
+    double *srt = (double *)malloc(sizeof(double) * (size_t)K);
+    for (int k = 0; k < K; ++k) {
+        double a = pi[k] - lam[k] * bi[k];
+        adj[k] = a > 0.0 ? a : 0.0;
+        srt[k] = adj[k];
+    }
+    qsort(srt, (size_t)K, sizeof(double), cmp_double_desc);
+    const double q_th = nth_largest(srt, K, Q);
+    const double q1_th = nth_largest(srt, K, Q + 1);
+    int64_t m = 0;
+    for (int k = 0; k < K; ++k) {
+        const double pbar = adj[k] >= q_th ? q1_th : q_th;
+        if (pi[k] > pbar && bi[k] > 0.0) {
+            ek[m] = k;
+            ev1[m] = (pi[k] - pbar) / bi[k];
+            ev2[m] = bi[k];
+            ++m;
+        }
+    }
+    *n = m;
+    free(adj);
+    free(srt);
+}
+
+/* One iteration of Algorithm 4 with Algorithm 5 as its Map: p and bd are    */
+/* [N][K] (bd[i][k] = b_ikk); lam_next[k] = the Reduce of the pairs of k.    */
+/* Returns the number of emitted pairs, or -1 on allocation failure.         */
+int64_t kpo_alg5_step(int64_t N, int K, const double *p, const double *bd,
+                      int Q, const double *lam, const double *B,
+                      double *lam_next)
+{
+    int64_t cap = N * (int64_t)K;
+    int32_t *ek = (int32_t *)malloc(sizeof(int32_t) * (size_t)(cap > 0 ? cap : 1));
+    double *v1 = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+    double *v2 = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+    int64_t *cnt = (int64_t *)calloc((size_t)K + 1, sizeof(int64_t));
+    if (!ek || !v1 || !v2 || !cnt) {
+        free(ek);
+        free(v1);
+        free(v2);
+        free(cnt);
+        return -1;
+    }
+    int64_t total = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t m = 0;
+        kpo_alg5_map_user(K, p + i * K, bd + i * K, Q, lam, &m, ek + total,
+                          v1 + total, v2 + total);
+        total += m;
+    }
+    /* group the pairs by k (the shuffle of the MapReduce), then Reduce */
+    for (int64_t e = 0; e < total; ++e)
+        cnt[ek[e] + 1]++;
+    for (int k = 0; k < K; ++k)
+        cnt[k + 1] += cnt[k];
+    double *g1 = (double *)malloc(sizeof(double) * (size_t)(total > 0 ? total : 1));
+    double *g2 = (double *)malloc(sizeof(double) * (size_t)(total > 0 ? total : 1));
+    int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    if (!g1 || !g2 || !pos) {
+        free(ek);
+        free(v1);
+        free(v2);
+        free(cnt);
+        free(g1);
+        free(g2);
+        free(pos);
+        return -1;
+    }
+    for (int k = 0; k < K; ++k)
+        pos[k] = cnt[k];
+    for (int64_t e = 0; e < total; ++e) {
+        const int64_t s = pos[ek[e]]++;
+        g1[s] = v1[e];
+        g2[s] = v2[e];
+    }
+    for (int k = 0; k < K; ++k)
+        lam_next[k] = kpo_scd_reduce(cnt[k + 1] - cnt[k], g1 + cnt[k], g2 + cnt[k], B[k]);
+    free(ek);
+    free(v1);
+    free(v2);
+    free(cnt);
+    free(g1);
+    free(g2);
+    free(pos);
+    return total;
 }
 
 int kpo_num_threads(void)

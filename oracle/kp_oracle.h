@@ -34,6 +34,12 @@ int64_t kpo_scd_step(int64_t N, int M, int K, const double *p, const double *b,
 int64_t kpo_postprocess(int64_t N, int M, int K, const double *p,
                         const double *b, const double *lam, const double *B,
                         int *x);
+void kpo_alg5_map_user(int K, const double *pi, const double *bi, int Q,
+                       const double *lam, int64_t *n, int32_t *ek,
+                       double *ev1, double *ev2);
+int64_t kpo_alg5_step(int64_t N, int K, const double *p, const double *bd,
+                      int Q, const double *lam, const double *B,
+                      double *lam_next);
 int kpo_num_threads(void);
 
 #endif

@@ -283,6 +283,23 @@ def regular_csr(N, M, K, C, seed, device="cpu", frac=0.1) -> Instance:
                     seed=seed, recipe="test instance (regular csr)")
 
 
+def one_to_one(N, K, Q, seed, device="cpu", frac=0.2) -> Instance:
+    """Sec. 5.1's special case: M = K items per user, item k consuming only
+    knapsack k (CSR with one entry per item, k = j), at most Q items per user.
+    p, b ~ U[0,1]; B_k = frac * sum_i b_ikk."""
+    g = _gen(device, seed)
+    p = torch.empty(N * K, dtype=torch.float32, device=device).uniform_(0.0, 1.0, generator=g)
+    val = torch.empty(N * K, dtype=torch.float32, device=device).uniform_(0.0, 1.0, generator=g)
+    kidx = torch.arange(K, dtype=torch.int16, device=device).repeat(N)
+    B = torch.clamp(val.view(N, K).double().sum(0) * frac, min=1e-3)
+    item_nnz = torch.ones(N * K, dtype=torch.uint8, device=device)
+    user_off = torch.arange(N + 1, dtype=torch.int64, device=device) * K
+    S, C = _groups(K, [], [], Q)
+    return Instance(name=f"one_to_one_{N}_{K}_Q{Q}", N=N, M=K, K=K, layout="csr", p=p, B=B, S=S, C=C,
+                    user_off=user_off, item_nnz=item_nnz, val=val, kidx=kidx, seed=seed,
+                    recipe="Sec. 5.1 special case (one item per knapsack, one cap)")
+
+
 WORKLOADS = {
     "dense_N1e4_M10_K5": small_dd_scd,
     "dense_N1e6_M20_K20": hier_m20,

@@ -112,6 +112,29 @@ def _scd_gpu(prob, lam):
     return ln.cpu().numpy()
 
 
+@pytest.mark.parametrize("K,Q,frac", [(10, 3, 0.2), (16, 1, 0.03), (8, 8, 0.2)])
+def test_scd_step_one_item_per_knapsack(K, Q, frac):
+    """Sec. 5.1's special case (M = K, item k consumes only knapsack k, at most Q
+    items; Q = K: the cap never binds): five GPU SCD steps from lambda = 0, each
+    against Algorithm 5's Map with Algorithm 4's Reduce at the GPU's lambda^t."""
+    N = 20_000
+    inst = gen.one_to_one(N, K, Q, seed=31 + K, device="cuda", frac=frac)
+    prob = _problem(inst)
+    p = inst.p.view(N, K).double().cpu().numpy()
+    bd = inst.val.view(N, K).double().cpu().numpy()
+    B = inst.B.cpu().numpy()
+    b3 = np.zeros((N, K, K))
+    for k in range(K):
+        b3[:, k, k] = bd[:, k]
+    lam = np.zeros(K)
+    for t in range(5):
+        got = _scd_gpu(prob, lam)
+        want = oracle.alg5_step(p, bd, Q, lam, B)
+        ok = lam_close_fp32(got, want, p, b3, lam)
+        assert ok.all(), (t, got[~ok], want[~ok])
+        lam = got
+
+
 @pytest.mark.parametrize("layout", ["dense", "csr"])
 @pytest.mark.parametrize("seed", [11, 12, 13, 14])
 def test_scd_step_parity_random(layout, seed):

@@ -419,3 +419,102 @@ def test_presolve_scaling_on_a_doubled_instance():
     # the whole instance as the sample: plain SCD on it
     full = oracle.presolve(p, b, S, C, B, np.arange(N), 3)
     assert np.allclose(full, lam, rtol=0, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 5 (Sec. 5.1): one item per knapsack, one cap Q
+# ---------------------------------------------------------------------------
+
+def _one_to_one(rng, K):
+    p = rng.uniform(0, 1, size=K)
+    bd = rng.uniform(0.05, 1, size=K)
+    b = np.zeros((K, K))
+    np.fill_diagonal(b, bd)
+    return p, bd, b
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_alg5_map_equals_general_map(seed):
+    """Algorithm 5 emits what Algorithms 3-4 emit when item k alone consumes
+    knapsack k and one set caps the count at Q (including Q >= K, where the cap
+    never binds, and multipliers that push items to zero profit)."""
+    rng = np.random.default_rng(seed)
+    K = int(rng.integers(1, 13))
+    Q = int(rng.integers(1, K + 2))
+    p, bd, b = _one_to_one(rng, K)
+    S, C = [(1 << K) - 1], [Q]
+    for _ in range(10):
+        lam = rng.uniform(0, 1.5, size=K) * (rng.random(K) < 0.7)
+        k5, v15, v25 = oracle.alg5_map_user(p, bd, Q, lam)
+        kg, v1g, v2g = oracle.scd_map_user(p, b, S, C, lam)
+        og = np.lexsort((v1g, kg))
+        o5 = np.lexsort((v15, k5))
+        assert np.array_equal(k5[o5], kg[og])
+        assert np.allclose(v15[o5], v1g[og], rtol=1e-12, atol=0)
+        assert np.array_equal(v25[o5], v2g[og])
+
+
+def test_alg5_without_binding_cap_is_the_zero_crossing():
+    """Q >= K: every item with p_k > 0 is taken while its adjusted profit is
+    positive, so its only breakpoint is p_k / b_kk (Eq. (11)-(13) without (3))."""
+    rng = np.random.default_rng(5)
+    K = 7
+    p, bd, _ = _one_to_one(rng, K)
+    for Q in (K, K + 3):
+        k5, v1, v2 = oracle.alg5_map_user(p, bd, Q, rng.uniform(0, 1, size=K))
+        assert np.array_equal(k5, np.arange(K))
+        assert np.allclose(v1, p / bd, rtol=1e-15)
+        assert np.array_equal(v2, bd)
+
+
+def test_alg5_single_item_cap_threshold():
+    """Q = 1: item k takes the user's single slot while p_k - lambda_k b_kk beats
+    the best other adjusted profit a*, so its breakpoint is (p_k - a*) / b_kk."""
+    p = np.array([0.9, 0.5, 0.2])
+    bd = np.array([0.5, 0.25, 1.0])
+    lam = np.array([1.0, 0.4, 0.0])
+    # adjusted profits: 0.4, 0.4, 0.2 (item 0 ranks first on ties: lower index)
+    k5, v1, v2 = oracle.alg5_map_user(p, bd, 1, lam)
+    want = {0: (0.9 - 0.4) / 0.5, 1: (0.5 - 0.4) / 0.25}
+    assert sorted(k5.tolist()) == [0, 1]
+    for k, v in zip(k5, v1):
+        assert v == pytest.approx(want[int(k)], rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_alg5_step_equals_general_step(seed):
+    """One Algorithm 4 iteration with Algorithm 5 as Map reaches the same
+    multipliers as with the general Map (same Reduce)."""
+    rng = np.random.default_rng(100 + seed)
+    N, K, Q = 300, int(rng.integers(2, 9)), int(rng.integers(1, 4))
+    p = rng.uniform(0, 1, size=(N, K))
+    bd = rng.uniform(0.05, 1, size=(N, K))
+    b = np.zeros((N, K, K))
+    for k in range(K):
+        b[:, k, k] = bd[:, k]
+    B = 0.2 * bd.sum(axis=0)
+    lam = np.zeros(K)
+    for _ in range(4):
+        got = oracle.alg5_step(p, bd, Q, lam, B)
+        want, _, _ = oracle.scd_step(p, b, [(1 << K) - 1], [Q], lam, B)
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-15)
+        lam = got
+
+
+def test_one_to_one_instance_layout():
+    """The seeded generator of Sec. 5.1's special case stores item k's only entry
+    in knapsack k, with one cap of Q over all items (layout check, CPU)."""
+    from paper_2002_00352_gb300 import gen
+    inst = gen.one_to_one(50, 6, 2, seed=3)
+    p, b = inst.to_dense_numpy()
+    bd = inst.val.view(50, 6).double().numpy()
+    for k in range(6):
+        assert np.array_equal(b[:, k, k], bd[:, k])
+    off = b.copy()
+    for k in range(6):
+        off[:, k, k] = 0
+    assert not off.any()
+    assert inst.S == [(1 << 6) - 1] and inst.C == [2]
+    want = oracle.alg5_step(p, bd, 2, np.zeros(6), inst.B.numpy())
+    got, _, _ = oracle.scd_step(p, b, inst.S, inst.C, np.zeros(6), inst.B.numpy())
+    assert np.allclose(got, want, rtol=1e-12)
