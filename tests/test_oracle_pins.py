@@ -518,3 +518,34 @@ def test_one_to_one_instance_layout():
     want = oracle.alg5_step(p, bd, 2, np.zeros(6), inst.B.numpy())
     got, _, _ = oracle.scd_step(p, b, inst.S, inst.C, np.zeros(6), inst.B.numpy())
     assert np.allclose(got, want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_postprocess_shortest_prefix_by_enumeration(seed):
+    """Sec. 5.4 on values from a coarse dyadic grid (all sums exact in FP64, many
+    equal group profits): the oracle resets exactly the shortest prefix of the
+    order (group profit, user index) after which every budget holds, found here
+    by enumerating every prefix length."""
+    rng = np.random.default_rng(200 + seed)
+    N, M, K = 40, 3, 2
+    p = rng.integers(0, 8, size=(N, M)) / 8.0
+    b = rng.integers(0, 8, size=(N, M, K)) / 8.0
+    lam = rng.integers(0, 4, size=K) / 4.0
+    x = (rng.random((N, M)) < 0.6).astype(np.int32)
+    R = np.einsum("nmk,nm->k", b, x)
+    B = np.maximum(np.floor(R * rng.uniform(0.3, 0.9, size=K)), 1.0)
+    q = np.einsum("nm,nm->n", p, x) - np.einsum("nmk,nm,k->n", b, x, lam)
+    order = np.lexsort((np.arange(N), q))
+    want = None
+    for r in range(N + 1):
+        keep = np.ones(N, dtype=bool)
+        keep[order[:r]] = False
+        if np.all(np.einsum("nmk,nm->k", b[keep], x[keep]) <= B):
+            want = r
+            break
+    x2, nreset = oracle.postprocess(p, b, lam, B, x)
+    assert nreset == want
+    reset = np.zeros(N, dtype=bool)
+    reset[order[:want]] = True
+    assert np.array_equal(x2[reset], np.zeros_like(x2[reset]))
+    assert np.array_equal(x2[~reset], x[~reset])
