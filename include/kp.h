@@ -28,6 +28,11 @@
  *     (Eq. (10)).  Kernels round lambda to FP32 once per call; reduced costs
  *     and breakpoints are computed in FP32, all sums over users in FP64 or
  *     exact 64-bit fixed point.
+ *   - Consumption b is summed in units of 2^-s, each entry rounded once to
+ *     the nearest unit, with s = min(40, 30 - ceil(log2 max b),
+ *     floor(62 - log2(entries * max b))) chosen at kp_create: the largest b
+ *     keeps 30 bits unless it is below 2^-10, and entries below 2^-41 count
+ *     as 0.
  *   - Calls on one handle must be ordered on one stream (they share the
  *     handle's scratch).
  *   - Return value: KP_OK, or an error code with nothing written to any
