@@ -30,9 +30,9 @@
  *     exact 64-bit fixed point.
  *   - Consumption b is summed in units of 2^-s, each entry rounded once to
  *     the nearest unit, with s = min(40, 30 - ceil(log2 max b),
- *     floor(62 - log2(entries * max b))) chosen at kp_create: the largest b
- *     keeps 30 bits unless it is below 2^-10, and entries below 2^-41 count
- *     as 0.
+ *     floor(62 - log2(entries * max b + 1))) (at least -120) chosen at
+ *     kp_create: the largest b keeps 30 bits unless it is below 2^-10, and
+ *     with s = 40 entries up to 2^-41 count as 0.
  *   - Calls on one handle must be ordered on one stream (they share the
  *     handle's scratch).
  *   - Return value: KP_OK, or an error code with nothing written to any
