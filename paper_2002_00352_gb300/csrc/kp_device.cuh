@@ -178,7 +178,7 @@ __device__ __forceinline__ uint32_t key_of(float v) {
 }
 
 // Mass of one entry in units of 2^-fixs: round(v * 2^fixs) (to nearest even),
-// below 2^30 for every b of the instance (Params::bscale = 2^fixs): the
+// at most 2^30 for every b of the instance (Params::bscale = 2^fixs): the
 // scaling is exact and the conversion is a single 32-bit one.
 __device__ __forceinline__ unsigned long long bmass(float v, float bscale) {
     return (unsigned long long)__float2uint_rn(v * bscale);

@@ -69,7 +69,7 @@ struct Params {
     const int16_t *kidx;
     const double *B;
     int32_t fixs;              // fixed-point shift of b sums: units of 2^-fixs
-    float bscale;              // 2^fixs: the mass of an entry is round(b * bscale) < 2^30
+    float bscale;              // 2^fixs: the mass of an entry is round(b * bscale) <= 2^30
     int32_t fixo;              // fixed-point shift of the objective sums
     int32_t tile;              // dense: users per shared-memory tile
     int32_t creg;              // CSR: every item has exactly creg entries (0: not regular)
@@ -128,8 +128,9 @@ __host__ __device__ inline int pair_first(uint32_t y, int t) { return (int)((y >
 __host__ __device__ inline int pair_second(uint32_t y, int t) { return (int)((y >> (10 * t + 5)) & 31u); }
 
 // Fixed-point unit 2^-s of the b masses: the mass round(b * 2^s) of one entry
-// stays below 2^30 (one 32-bit conversion per entry) and every per-knapsack
-// sum over `count` entries below 2^62.
+// stays at most 2^30 (equal when max b is a power of two; one 32-bit
+// conversion per entry) and every per-knapsack sum over `count` entries below
+// 2^62.
 inline int mass_shift(double count, float maxb) {
     const double lb = maxb > 0.f ? std::log2((double)maxb) : -200.0;
     const int s1 = (int)std::floor(62.0 - std::log2(count * (double)maxb + 1.0));
