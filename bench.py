@@ -182,6 +182,39 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def quality(inst, prob, x_after, R_before, R_after, g, primal_before):
+    """Solution quality at the last lambda (Sec. 6.1-6.2): duality gap (dual value minus
+    primal objective), the number of knapsacks over budget and the max constraint
+    violation ratio (excess over budget / budget), for x = Algorithm 1 at lambda and
+    after Sec. 5.4's post-processing (x_after)."""
+    import torch
+    from paper_2002_00352_gb300 import kp
+    B = inst.B
+    N, M = inst.N, inst.M
+    pv = inst.p.view(N, M)
+    W = (M + 31) // 32
+    xw = x_after.view(N, W)
+    primal_after = 0.0
+    step = 1 << 24
+    for s in range(0, N, step):
+        n = min(step, N - s)
+        xs = kp.unpack_x(xw[s:s + n].reshape(-1), n, M).double()
+        primal_after += float((xs * pv[s:s + n].double()).sum())
+
+    def viol(R):
+        r = torch.clamp((R - B) / B, min=0.0)
+        return int((R > B).sum()), float(r.max())
+
+    nb, mb = viol(R_before)
+    na, ma = viol(R_after)
+    return {"dual_value": g, "primal_before": primal_before, "duality_gap_before": g - primal_before,
+            "violated_before": nb, "max_violation_ratio_before": mb,
+            "primal_after": primal_after, "duality_gap_after": g - primal_after,
+            "violated_after": na, "max_violation_ratio_after": ma,
+            "note": "at the lambda after the timed steps; primal after post-processing summed here "
+                    "(torch, float64) from the returned x"}
+
+
 def cpu_baseline(inst, n, min_seconds=10.0):
     """The oracle as it stands on the first n users of the same instance (budgets
     scaled by n/N): SCD iterations, each a state pass (Algorithms 1-2) plus a
@@ -352,15 +385,16 @@ def main():
           for _ in range(args.steps)]
     cur = [0]
 
-    def step(i=None):
+    def step(i=None, h=None):
+        h = prob if h is None else h
         a, b = lam[cur[0]], lam[1 - cur[0]]
         if i is not None:
             ev[i][0].record(stream)
-        kp.kp_scd_breakpoints(prob, a, R=R, dual_sum=dsum, primal_sum=psum, x_bits=xb)
+        kp.kp_scd_breakpoints(h, a, R=R, dual_sum=dsum, primal_sum=psum, x_bits=xb)
         if i is not None:
             ev[i][1].record(stream)
-        kp.kp_threshold_select(prob, a, b)
-        kp.kp_dual_backward(prob, a, xb, R, up, grad_lambda=gl, grad_p=gp, grad_B=gB)
+        kp.kp_threshold_select(h, a, b)
+        kp.kp_dual_backward(h, a, xb, R, up, grad_lambda=gl, grad_p=gp, grad_B=gB)
         cur[0] = 1 - cur[0]
 
     for _ in range(args.warmup):
@@ -403,8 +437,26 @@ def main():
                 "kernel_ms": k_ms, "algo_bytes_per_user": per_user,
                 "peak_source": f"{peak_kind} hbm_gbs"}
 
-    # select statistics of the timed steps (passes per step include re-runs)
-    out_stats = None
+    # second kernel: the DD / state pass (kp_reduce_consumption: Algorithms 1-2) at the
+    # last lambda, timed alone on the same stream
+    lam_f = lam[cur[0]]
+    st_ms = []
+    for rep in range(6):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        kp.kp_reduce_consumption(prob, lam_f, R=R, dual_sum=dsum, primal_sum=psum)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep >= 2:
+            st_ms.append(e0.elapsed_time(e1))
+    s_ms = statistics.mean(st_ms)
+    s_ach = N * per_user / (s_ms / 1e3) / 1e9
+    roofline_state = {"bound": "hbm", "achieved": s_ach, "peak": peak, "unit": "GB/s",
+                      "frac": s_ach / peak, "traffic": None,
+                      "kernel": "user pass, state mode (csr_pass_kernel MODE_STATE) + finalize",
+                      "kernel_ms": s_ms, "algo_bytes_per_user": per_user,
+                      "peak_source": f"{peak_kind} hbm_gbs"}
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
@@ -416,7 +468,7 @@ def main():
                          "l2": "inputs (%.1f GB) exceed L2 (129 MB); no flush" % (inst.nbytes() / 1e9),
                          "parallelism": "replicas" if world > 1 else "single GPU",
                          "lambda0": 0.0},
-              "roofline": roofline, "clocks": clocks,
+              "roofline": roofline, "roofline_state_pass": roofline_state, "clocks": clocks,
               # per step: pass + finalize + select, 4 x (select + re-run pass), backward;
               # and the rare-knapsack kernel after each of the 5 passes when the instance has some
               "gpu_launches": args.steps * (3 + 2 * 4 + 1 + (5 if kp.kp_info(prob)["rare_blocks"] > 0 else 0))}
@@ -447,7 +499,10 @@ def main():
                 pp_ms.append(e0.elapsed_time(e1))
         kp.kp_device_status(prob)
         R_b = torch.empty_like(R_a)
-        kp.kp_reduce_consumption(prob, lam_f, R=R_b)
+        g_b = torch.zeros((), dtype=torch.float64, device=dev)
+        pr_b = torch.zeros((), dtype=torch.float64, device=dev)
+        kp.kp_reduce_consumption(prob, lam_f, R=R_b, primal_sum=pr_b, g=g_b)
+        result["quality"] = quality(inst, prob, x_w, R_b, R_a, float(g_b), float(pr_b))
         result["postprocess"] = {
             "ms": statistics.mean(pp_ms), "users_reset": int(reset),
             "over_budget_before": int((R_b > inst.B).sum()),
@@ -456,10 +511,13 @@ def main():
                     "radix selection of the last user reset, no sort"}
         del x_f, x_w
 
-    # end to end through the public API from pinned host memory
+    # end to end through the public API from pinned host memory: a fresh job (the
+    # instance copied in, a new handle created, SCD from lambda = 0)
     if not args.no_e2e and rank == 0:
+        prob.close()
+        torch.cuda.empty_cache()
         host = {}
-        names = ["p", "b", "user_off", "item_nnz", "val", "kidx"]
+        names = ["p", "b", "user_off", "item_nnz", "val", "kidx", "B"]
         for nm in names:
             t = getattr(inst, nm)
             if t is not None:
@@ -469,28 +527,35 @@ def main():
         h2d = sum(h.numel() * h.element_size() for h in host.values())
         lam_h = torch.zeros(K, dtype=torch.float64, pin_memory=True)
         R_h = torch.zeros(K, dtype=torch.float64, pin_memory=True)
+        for nm in names:  # the device copies start out empty
+            t = getattr(inst, nm)
+            if t is not None:
+                t.zero_()
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        t0 = time.perf_counter()
         for nm, h in host.items():
             getattr(inst, nm).copy_(h, non_blocking=True)
+        torch.cuda.synchronize()
+        prob2 = kp.kp_create_from_instance(inst)   # validation scan, CSR structure, scratch
         lam[0].zero_()
         cur[0] = 0
         for i in range(args.steps):
-            step()
+            step(h=prob2)
         lam_h.copy_(lam[cur[0]], non_blocking=True)
         R_h.copy_(R, non_blocking=True)
-        e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1)
-        result["e2e"] = {"value": N * args.steps / (e_ms / 1e3), "unit": UNIT,
-                         "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 2 * K * 8,
-                         "note": "a job of `steps` SCD iterations from lambda = 0 through the C ABI: "
-                                 "instance copied host->device (pinned) once per job, lambda and R "
-                                 "read back at the end; unlike `value` it includes the first "
-                                 "iterations, whose thresholds lie far from any prediction and "
-                                 "take re-run passes"}
+        e_s = time.perf_counter() - t0
+        kp.kp_device_status(prob2)
+        prob2.close()
+        result["e2e"] = {"value": N * args.steps / e_s, "unit": UNIT,
+                         "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": 2 * K * 8 / args.steps,
+                         "seconds": e_s,
+                         "note": "a fresh job of `steps` SCD iterations (+ backward) from lambda = 0 through "
+                                 "the C ABI, host wall clock: the instance copied host->device from pinned "
+                                 "memory, kp_create (validation scan, CSR structure, scratch) on a new "
+                                 "handle whose threshold prediction starts cold, lambda and R read back; "
+                                 "unlike `value` it includes the first iterations, whose thresholds lie far "
+                                 "from any prediction and take re-run passes"}
     if not args.no_cpu and rank == 0:
         try:
             result["cpu_baseline"] = cpu_baseline(inst, min(args.cpu_sample, N))

@@ -295,6 +295,11 @@ kp_status kp_postprocess(kp_problem *h, const double *lambda, uint32_t *x_bits, 
  * out[3] = breakpoint-buffer entries per (knapsack, block). */
 kp_status kp_info(kp_problem *h, int64_t out[4]);
 
+/* Limits of this implementation (host values, no device work): out[0] =
+ * KP_MAX_M, out[1] = KP_MAX_L, out[2] = KP_MAX_K.  KP_EINVAL if out is NULL.
+ * (Not in the paper.) */
+kp_status kp_limits(int32_t out[3]);
+
 /* Thread-local description of the last error on this thread. */
 const char *kp_last_error(void);
 

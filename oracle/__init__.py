@@ -64,6 +64,8 @@ def _load():
     lib.kpo_scd_reduce.restype = f64
     lib.kpo_scd_step.argtypes = [i64, i32, i32, P, P, i32, P, P, P, P, P, P, P]
     lib.kpo_scd_step.restype = i64
+    lib.kpo_scd_map_all.argtypes = [i64, i32, i32, P, P, i32, P, P, P, i64, P, P, P, P]
+    lib.kpo_scd_map_all.restype = i64
     lib.kpo_postprocess.argtypes = [i64, i32, i32, P, P, P, P, P]
     lib.kpo_postprocess.restype = i64
     lib.kpo_alg5_map_user.argtypes = [i32, P, P, i32, P, P, P, P, P]
@@ -184,6 +186,34 @@ def scd_map_user(p_i, b_i, S, C, lam):
     return ek[:m].copy(), v1[:m].copy(), v2[:m].copy()
 
 
+def scd_map_users(p, b, S, C, lam, users=None):
+    """Algorithms 3-4 Map for every user (or the listed ones): arrays (user, k, v1, v2)
+    of all emitted pairs, users ascending (kpo_scd_map_all: scd_map_user per user)."""
+    p, b, lam = _f64(p), _f64(b), _f64(lam)
+    S, C = _tree(S, C)
+    idx = None if users is None else np.asarray(users, dtype=np.int64)
+    if idx is not None:
+        p, b = _f64(p[idx]), _f64(b[idx])
+    N, M, K = b.shape
+    cap = max(1024, 4 * N * K)
+    while True:
+        eu = np.zeros(cap, dtype=np.int64)
+        ek = np.zeros(cap, dtype=np.int32)
+        v1 = np.zeros(cap)
+        v2 = np.zeros(cap)
+        n = _load().kpo_scd_map_all(N, M, K, _ptr(p), _ptr(b), len(S), _ptr(S), _ptr(C), _ptr(lam),
+                                    cap, _ptr(eu), _ptr(ek), _ptr(v1), _ptr(v2))
+        if n < 0:
+            raise MemoryError("oracle scd_map_all: allocation failed")
+        if n <= cap:
+            break
+        cap = int(n)
+    eu = eu[:n]
+    if idx is not None:
+        eu = idx[eu]
+    return eu.copy(), ek[:n].copy(), v1[:n].copy(), v2[:n].copy()
+
+
 def scd_reduce(v1, v2, Bk) -> float:
     """Algorithm 4 Reduce for one knapsack."""
     v1, v2 = _f64(v1), _f64(v2)
@@ -242,6 +272,19 @@ def alg5_map_user(p_i, bdiag_i, Q, lam):
                               _ptr(ek), _ptr(v1), _ptr(v2))
     m = n.value
     return ek[:m].copy(), v1[:m].copy(), v2[:m].copy()
+
+
+def alg5_map_users(p, bdiag, Q, lam):
+    """Algorithm 5 for every user (p, bdiag [N, K]): arrays (user, k, v1, v2)."""
+    p, bdiag = _f64(p), _f64(bdiag)
+    us, ks, v1s, v2s = [], [], [], []
+    for i in range(p.shape[0]):
+        k, v1, v2 = alg5_map_user(p[i], bdiag[i], Q, lam)
+        us.append(np.full(len(k), i, dtype=np.int64))
+        ks.append(k)
+        v1s.append(v1)
+        v2s.append(v2)
+    return np.concatenate(us), np.concatenate(ks), np.concatenate(v1s), np.concatenate(v2s)
 
 
 def alg5_step(p, bdiag, Q, lam, B):

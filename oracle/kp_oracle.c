@@ -513,6 +513,93 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* The Map of Algorithm 4 for every user (kpo_scd_map_user per user, users   */
+/* split over threads, lists concatenated in thread order, so users ascend): */
+/* writes (user, k, v1, v2) of every emission when the total fits in cap and */
+/* returns the total (or -1 on allocation failure); no Reduce.               */
+/* ------------------------------------------------------------------------ */
+int64_t kpo_scd_map_all(int64_t N, int M, int K, const double *p, const double *b,
+                        int L, const uint64_t *S, const int *C, const double *lam,
+                        int64_t cap_out, int64_t *eu, int32_t *ek, double *ev1,
+                        double *ev2)
+{
+    int topo[64];
+    kpo_topo_order(L, S, topo);
+    int64_t per_user = (int64_t)K * (M + (int64_t)M * (M - 1) / 2);
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    int64_t *cnt = (int64_t *)calloc((size_t)nth, sizeof(int64_t));
+    int64_t **tu = (int64_t **)calloc((size_t)nth, sizeof(int64_t *));
+    int32_t **tk = (int32_t **)calloc((size_t)nth, sizeof(int32_t *));
+    double **t1 = (double **)calloc((size_t)nth, sizeof(double *));
+    double **t2 = (double **)calloc((size_t)nth, sizeof(double *));
+    int64_t *cap = (int64_t *)calloc((size_t)nth, sizeof(int64_t));
+    int failed = 0;
+#pragma omp parallel num_threads(nth)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < N; ++i) {
+            if (cnt[tid] + per_user > cap[tid]) {
+                int64_t nc = 2 * cap[tid] + 4 * per_user;
+                int64_t *nu = (int64_t *)realloc(tu[tid], sizeof(int64_t) * (size_t)nc);
+                if (nu) tu[tid] = nu;
+                int32_t *nk = (int32_t *)realloc(tk[tid], sizeof(int32_t) * (size_t)nc);
+                if (nk) tk[tid] = nk;
+                double *n1 = (double *)realloc(t1[tid], sizeof(double) * (size_t)nc);
+                if (n1) t1[tid] = n1;
+                double *n2 = (double *)realloc(t2[tid], sizeof(double) * (size_t)nc);
+                if (n2) t2[tid] = n2;
+                if (!nu || !nk || !n1 || !n2) {
+                    failed = 1;
+                    continue;
+                }
+                cap[tid] = nc;
+            }
+            int64_t before = cnt[tid];
+            kpo_scd_map_user(M, K, p + (size_t)i * M, b + (size_t)i * M * K, L,
+                             S, C, topo, lam, &cnt[tid], tk[tid], t1[tid],
+                             t2[tid]);
+            for (int64_t e = before; e < cnt[tid]; ++e)
+                tu[tid][e] = i;
+        }
+    }
+    int64_t total = 0;
+    for (int t = 0; t < nth; ++t)
+        total += cnt[t];
+    if (failed) {
+        total = -1;
+    } else if (total <= cap_out) {
+        int64_t o = 0;
+        for (int t = 0; t < nth; ++t)
+            for (int64_t e = 0; e < cnt[t]; ++e, ++o) {
+                eu[o] = tu[t][e];
+                ek[o] = tk[t][e];
+                ev1[o] = t1[t][e];
+                ev2[o] = t2[t][e];
+            }
+    }
+    for (int t = 0; t < nth; ++t) {
+        free(tu[t]);
+        free(tk[t]);
+        free(t1[t]);
+        free(t2[t]);
+    }
+    free(tu);
+    free(tk);
+    free(t1);
+    free(t2);
+    free(cnt);
+    free(cap);
+    return total;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sec. 5.4: post-processing for feasibility (R7).  x is [N][M], modified in */
 /* place.  Returns the number of users reset.                                */
 /* ------------------------------------------------------------------------ */

@@ -31,6 +31,10 @@ int64_t kpo_scd_step(int64_t N, int M, int K, const double *p, const double *b,
                      int L, const uint64_t *S, const int *C, const double *lam,
                      const double *B, double *lam_next, int64_t *nemit,
                      double *mass);
+int64_t kpo_scd_map_all(int64_t N, int M, int K, const double *p, const double *b,
+                        int L, const uint64_t *S, const int *C, const double *lam,
+                        int64_t cap_out, int64_t *eu, int32_t *ek, double *ev1,
+                        double *ev2);
 int64_t kpo_postprocess(int64_t N, int M, int K, const double *p,
                         const double *b, const double *lam, const double *B,
                         int *x);

@@ -82,9 +82,10 @@ int kp_version(void) { return 100; }
 
 namespace kp_impl {
 
-// Validates the description and fills h->P (host checks, device scan, fixed-point
-// shifts, CSR shape); allocates nothing that outlives the call.
-kp_status prepare(const kp_desc *d, kp_problem *h) {
+// Validates the description and fills P (host checks; the device scan of the
+// instance into the caller's five flag words `flags`, on stream st, waited for;
+// fixed-point shifts; CSR shape).  Allocates nothing.
+kp_status fill_params(const kp_desc *d, kp::Params &P, uint32_t *flags, cudaStream_t st) {
     if (!d) return fail(KP_EINVAL, "NULL description");
     if (d->N < 1) return fail(KP_EINVAL, "N must be >= 1 (got %lld)", (long long)d->N);
     if (d->M < 1 || d->M > KP_MAX_M) return fail(KP_EINVAL, "M must be in 1..%d (got %d)", KP_MAX_M, d->M);
@@ -113,10 +114,7 @@ kp_status prepare(const kp_desc *d, kp_problem *h) {
             if (i != 0 && i != d->S[a] && i != d->S[b])
                 return fail(KP_EINVAL, "local sets %d and %d are neither disjoint nor nested", a, b);
         }
-    int cur_dev = 0;
-    KP_CUDA(cudaGetDevice(&cur_dev), "cudaGetDevice");
-    h->device = cur_dev;
-    kp::Params &P = h->P;
+    memset(&P, 0, sizeof(P));
     P.N = d->N;
     P.M = d->M;
     P.K = d->K;
@@ -130,7 +128,7 @@ kp_status prepare(const kp_desc *d, kp_problem *h) {
     P.kidx = d->csr_k;
     P.B = d->B;
     // topological order of the sets (subsets first: by size, ties by index)
-    std::vector<int> order(d->L);
+    int order[KP_MAX_L];
     for (int l = 0; l < d->L; ++l) order[l] = l;
     for (int a = 1; a < d->L; ++a) {
         int v = order[a], b = a - 1;
@@ -140,7 +138,6 @@ kp_status prepare(const kp_desc *d, kp_problem *h) {
         }
         order[b + 1] = v;
     }
-    memset(&P.tree, 0, sizeof(P.tree));
     P.tree.L = d->L;
     for (int t = 0; t < d->L; ++t) {
         int l = order[t];
@@ -151,85 +148,70 @@ kp_status prepare(const kp_desc *d, kp_problem *h) {
             if ((d->S[l] >> j) & 1ull) P.tree.ipath[j] |= 1u << t;
     }
 
-    kp_status st = KP_OK;
-    // device scan of the instance (Sec. 2 data assumptions)
-    uint32_t *flags = nullptr;
-    {
-        cudaError_t ea = cudaMalloc(&flags, 5 * sizeof(uint32_t));
-        if (ea != cudaSuccess) return fail(KP_ENOMEM, "cudaMalloc(validation flags): %s", cudaGetErrorString(ea));
-    }
-    {
-        const uint32_t init[5] = {0u, 0u, 0u, 0xffffffffu, 0u};
-        cudaError_t e0 = cudaMemcpy(flags, init, sizeof(init), cudaMemcpyHostToDevice);
-        if (e0 != cudaSuccess) {
-            st = cuda_fail(e0, "validation flags");
-            goto fail_out;
+    // device scan of the instance (Sec. 2 data assumptions); flags[3] starts at all ones
+    cudaError_t e = cudaMemsetAsync(flags, 0, 5 * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags + 3, 0xff, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = kp::launch_validate(P, flags, st);
+    uint32_t hf[5] = {0, 0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "validate");
+    if (hf[0])
+        return fail(KP_EDATA, "instance violates Sec. 2 assumptions:%s%s%s%s%s",
+                    (hf[0] & 1) ? " p negative or non-finite;" : "",
+                    (hf[0] & 2) ? " b negative or non-finite;" : "",
+                    (hf[0] & 4) ? " csr_user_off inconsistent with csr_item_nnz;" : "",
+                    (hf[0] & 8) ? " csr_k out of range or not increasing within an item;" : "",
+                    (hf[0] & 16) ? " B_k not positive and finite;" : "");
+    float maxb;
+    memcpy(&maxb, &hf[1], 4);
+    if (!(maxb < 0x1p100f))  // breakpoints divide by b with the fast reciprocal
+        return fail(KP_EDATA, "b values must be below 2^100 (max b = %g)", (double)maxb);
+    double count;
+    if (P.layout == KP_B_DENSE) {
+        count = (double)P.N * P.M;
+    } else {
+        int64_t ends[2] = {0, 0};
+        e = cudaMemcpyAsync(&ends[0], P.uoff, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&ends[1], P.uoff + P.N, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "csr offsets copy");
+        count = (double)(ends[1] - ends[0]);
+        P.uoff0 = ends[0];
+        if (hf[3] == hf[4] && (hf[3] == 1 || hf[3] == 2)) {
+            P.creg = (int)hf[3];
+            const bool mexact = P.M == 8 || P.M == 10 || P.M == 16;
+            const uintptr_t pp = (uintptr_t)P.p, vp = (uintptr_t)(P.val + P.uoff0),
+                            kp2 = (uintptr_t)(P.kidx + P.uoff0);
+            P.vec = mexact && (pp % 8 == 0) && (vp % 16 == 0) && (kp2 % 8 == 0) &&
+                    ((P.M * P.creg) % 4 == 0);
         }
     }
-    {
-        cudaError_t e = kp::launch_validate(P, flags, 0);
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) {
-            st = cuda_fail(e, "validate");
-            goto fail_out;
-        }
-        uint32_t hf[5] = {0, 0, 0, 0, 0};
-        e = cudaMemcpy(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) {
-            st = cuda_fail(e, "validate copy");
-            goto fail_out;
-        }
-        if (hf[0]) {
-            st = fail(KP_EDATA, "instance violates Sec. 2 assumptions:%s%s%s%s%s",
-                      (hf[0] & 1) ? " p negative or non-finite;" : "",
-                      (hf[0] & 2) ? " b negative or non-finite;" : "",
-                      (hf[0] & 4) ? " csr_user_off inconsistent with csr_item_nnz;" : "",
-                      (hf[0] & 8) ? " csr_k out of range or not increasing within an item;" : "",
-                      (hf[0] & 16) ? " B_k not positive and finite;" : "");
-            goto fail_out;
-        }
-        float maxb;
-        memcpy(&maxb, &hf[1], 4);
-        if (!(maxb < 0x1p100f)) {  // breakpoints divide by b with the fast reciprocal
-            st = fail(KP_EDATA, "b values must be below 2^100 (max b = %g)", (double)maxb);
-            goto fail_out;
-        }
-        double count;
-        if (P.layout == KP_B_DENSE) {
-            count = (double)P.N * P.M;
-        } else {
-            int64_t ends[2] = {0, 0};
-            e = cudaMemcpy(&ends[0], P.uoff, 8, cudaMemcpyDeviceToHost);
-            if (e == cudaSuccess) e = cudaMemcpy(&ends[1], P.uoff + P.N, 8, cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) {
-                st = cuda_fail(e, "csr offsets copy");
-                goto fail_out;
-            }
-            count = (double)(ends[1] - ends[0]);
-            P.uoff0 = ends[0];
-            if (hf[3] == hf[4] && (hf[3] == 1 || hf[3] == 2)) {
-                P.creg = (int)hf[3];
-                const bool mexact = P.M == 8 || P.M == 10 || P.M == 16;
-                const uintptr_t pp = (uintptr_t)P.p, vp = (uintptr_t)(P.val + P.uoff0),
-                                kp2 = (uintptr_t)(P.kidx + P.uoff0);
-                P.vec = mexact && (pp % 8 == 0) && (vp % 16 == 0) && (kp2 % 8 == 0) &&
-                        ((P.M * P.creg) % 4 == 0);
-            }
-        }
-        // fixed-point mass: every per-knapsack sum is below count * max b
-        P.fixs = kp::mass_shift(count, maxb);
-        P.bscale = std::ldexp(1.0f, P.fixs);
-        // objective sums: every per-user value is below M * max p
-        float maxp;
-        memcpy(&maxp, &hf[2], 4);
-        double bo = (double)P.N * P.M * (double)maxp + 1.0;
-        int so = (int)std::floor(62.0 - std::log2(bo));
-        if (so > 40) so = 40;
-        if (so < 0) so = 0;
-        P.fixo = so;
-    }
+    // fixed-point mass: every per-knapsack sum is below count * max b
+    P.fixs = kp::mass_shift(count, maxb);
+    P.bscale = std::ldexp(1.0f, P.fixs);
+    // objective sums: every per-user value is below M * max p
+    float maxp;
+    memcpy(&maxp, &hf[2], 4);
+    double bo = (double)P.N * P.M * (double)maxp + 1.0;
+    int so = (int)std::floor(62.0 - std::log2(bo));
+    if (so > 40) so = 40;
+    if (so < 0) so = 0;
+    P.fixo = so;
     P.tile = P.layout == KP_B_DENSE ? kp::dense_tile_users(P) : 0;
-fail_out:
+    return KP_OK;
+}
+
+// Validates the description and fills h->P; the flag words of the scan are
+// allocated for the call only.
+kp_status prepare(const kp_desc *d, kp_problem *h) {
+    int cur_dev = 0;
+    KP_CUDA(cudaGetDevice(&cur_dev), "cudaGetDevice");
+    h->device = cur_dev;
+    uint32_t *flags = nullptr;
+    cudaError_t ea = cudaMalloc(&flags, 5 * sizeof(uint32_t));
+    if (ea != cudaSuccess) return fail(KP_ENOMEM, "cudaMalloc(validation flags): %s", cudaGetErrorString(ea));
+    kp_status st = fill_params(d, h->P, flags, 0);
     cudaFree(flags);
     return st;
 }
@@ -512,6 +494,14 @@ kp_status kp_info(kp_problem *h, int64_t out[4]) {
     out[1] = h->S.nrare;
     out[2] = h->S.rare_grid;
     out[3] = h->S.cap_kb;
+    return KP_OK;
+}
+
+kp_status kp_limits(int32_t out[3]) {
+    if (!out) return fail(KP_EINVAL, "kp_limits: NULL argument");
+    out[0] = KP_MAX_M;
+    out[1] = KP_MAX_L;
+    out[2] = KP_MAX_K;
     return KP_OK;
 }
 

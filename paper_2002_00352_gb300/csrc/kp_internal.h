@@ -186,6 +186,9 @@ struct kp_problem {
 namespace kp_impl {
 // kp_api.cu: validation + parameters, and scratch for blocks [g_lo, g_lo + gspan)
 kp_status prepare(const kp_desc *d, kp_problem *h);
+// the checks and parameters of prepare, with the scan's five flag words given
+// by the caller (device memory) and run on stream st; allocates nothing
+kp_status fill_params(const kp_desc *d, kp::Params &P, uint32_t *flags, cudaStream_t st);
 kp_status alloc_scratch(kp_problem *h, int G, int g_lo, int gspan, double budget, kp::Counters *ctr,
                         uint32_t *bufcnt = nullptr);
 }  // namespace kp_impl

@@ -57,7 +57,7 @@ EXPORTS = [
     "kp_version",
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
-    "kp_autotune",
+    "kp_autotune", "kp_limits",
 ]
 
 
@@ -92,6 +92,7 @@ def load_library(path: Optional[str] = None):
     lib.kp_batch_scd_step.argtypes = [P, P, P, P]
     lib.kp_batch_device_status.argtypes = [P, P]
     lib.kp_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int32), P]
+    lib.kp_limits.argtypes = [ctypes.POINTER(ctypes.c_int32)]
     lib.kp_last_error.restype = ctypes.c_char_p
     lib.kp_version.restype = ctypes.c_int
     for name in EXPORTS:
@@ -323,6 +324,13 @@ def kp_info(prob: Problem) -> dict:
     out = (ctypes.c_int64 * 4)()
     _check(load_library().kp_info(prob.handle, out))
     return {"pass_blocks": out[0], "rare_users": out[1], "rare_blocks": out[2], "buffer_per_block": out[3]}
+
+
+def kp_limits() -> dict:
+    """Limits of the library (include/kp.h: KP_MAX_M, KP_MAX_L, KP_MAX_K)."""
+    out = (ctypes.c_int32 * 3)()
+    _check(load_library().kp_limits(out))
+    return {"max_m": out[0], "max_l": out[1], "max_k": out[2]}
 
 
 def kp_autotune(prob: Problem, stream=None) -> int:

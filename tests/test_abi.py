@@ -48,3 +48,12 @@ def test_library_loads_and_binding_covers_exports(lib_path):
 def test_sm103a_only(lib_path):
     from paper_2002_00352_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_limits_match_header(lib_path):
+    """kp_limits reports the enum of include/kp.h (host values, no device work)."""
+    src = open(os.path.join(ROOT, "include", "kp.h")).read()
+    want = {n: int(v) for n, v in re.findall(r"\b(KP_MAX_[MLK])\s*=\s*(\d+)", src)}
+    from paper_2002_00352_gb300 import kp
+    got = kp.kp_limits()
+    assert (got["max_m"], got["max_l"], got["max_k"]) == (want["KP_MAX_M"], want["KP_MAX_L"], want["KP_MAX_K"])

@@ -41,9 +41,9 @@ def test_mass_shift_bounds_and_maximality(probe):
         assert -120 <= s <= 40
         if s > -120:
             assert m * 2.0 ** s <= 2.0 ** 30, (c, m, s)
-            assert c * m * 2.0 ** s < 2.0 ** 62, (c, m, s)
-        if s < 40:  # one more bit breaks a bound
-            assert m * 2.0 ** (s + 1) > 2.0 ** 30 or c * m * 2.0 ** (s + 1) >= 2.0 ** 61, (c, m, s)
+            assert (c * m + 1) * 2.0 ** s <= 2.0 ** 62, (c, m, s)
+        if -120 < s < 40:  # one more bit breaks one of the two bounds the shift keeps
+            assert m * 2.0 ** (s + 1) > 2.0 ** 30 or (c * m + 1) * 2.0 ** (s + 1) > 2.0 ** 62, (c, m, s)
 
 
 def test_mass_shift_unit_scale_instance(probe):

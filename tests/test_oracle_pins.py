@@ -131,6 +131,37 @@ def test_scd_map_is_the_consumption_step_function(seed):
         assert _consumption_bf(p_i, b_i, S, C, lam, k, 1e9) == 0.0
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_scd_map_all_users_is_each_users_step_function(seed):
+    """The all-users listing of the Map (users split over threads) describes every
+    listed user's k-consumption step function, checked by exhaustive search as
+    above, and its Reduce per k is the step of Algorithm 4."""
+    rng = np.random.default_rng(900 + seed)
+    N = 7
+    M = int(rng.integers(1, 7))
+    K = int(rng.integers(1, 4))
+    S, C = random_laminar(M, rng)
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, K)) * (rng.random((N, M, K)) < 0.7)
+    lam = rng.uniform(0, 0.8, size=K)
+    eu, ek, v1, v2 = oracle.scd_map_users(p, b, S, C, lam)
+    assert np.all(np.diff(eu) >= 0)
+    for i in range(N):
+        for k in range(K):
+            sel = (eu == i) & (ek == k)
+            for lk in rng.uniform(0, 3.0, size=10):
+                if sel.any() and np.min(np.abs(v1[sel] - lk)) < 1e-9:
+                    continue
+                want = _consumption_bf(p[i], b[i], S, C, lam, k, lk)
+                assert float(v2[sel & (v1 > lk)].sum()) == pytest.approx(want, abs=1e-9)
+    B = rng.uniform(0.2, 2.0, size=K)
+    step, _, _ = oracle.scd_step(p, b, S, C, lam, B)
+    for k in range(K):
+        assert oracle.scd_reduce(v1[ek == k], v2[ek == k], B[k]) == step[k]
+    sub = oracle.scd_map_users(p, b, S, C, lam, users=[5, 2])
+    assert set(sub[0].tolist()) <= {2, 5}
+
+
 def test_scd_map_single_item_closed_form():
     """One item, one knapsack, no local constraint: the only breakpoint is the zero
     crossing p/b, with jump b (Algorithm 3's zero-crossing candidate)."""

@@ -67,4 +67,4 @@ def test_noalloc_rejects_too_many_knapsacks():
 
 
 def kp_max_k():
-    return 2048
+    return kp.kp_limits()["max_k"]
