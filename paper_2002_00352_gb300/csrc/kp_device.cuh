@@ -180,8 +180,8 @@ __device__ __forceinline__ uint32_t key_of(float v) {
 // Mass of one entry in units of 2^-fixs: round(v * 2^fixs) (to nearest even),
 // at most 2^30 for every b of the instance (Params::bscale = 2^fixs): the
 // scaling is exact and the conversion is a single 32-bit one.
-__device__ __forceinline__ unsigned long long bmass(float v, float bscale) {
-    return (unsigned long long)__float2uint_rn(v * bscale);
+__device__ __forceinline__ uint32_t bmass(float v, float bscale) {
+    return __float2uint_rn(v * bscale);
 }
 
 // round(v * 2^s) for finite v >= 0, with integer operations only (on GB300
@@ -537,11 +537,6 @@ __device__ void sweep_k(const float *pt, int ps, const float *s, int ss, int M, 
 // ---------------------------------------------------------------------------
 // shared-memory atomics through the shared state space (never generic)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void shared_add_u64(unsigned long long *p, unsigned long long v) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
-}
-
 __device__ __forceinline__ uint32_t shared_inc_u32(uint32_t *p) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(p);
     uint32_t old;
@@ -549,12 +544,54 @@ __device__ __forceinline__ uint32_t shared_inc_u32(uint32_t *p) {
     return old;
 }
 
-// red.shared.add.u64 executed only where cond != 0 (predicated, no branch)
-__device__ __forceinline__ void shared_add_u64_if(unsigned long long *p, unsigned long long v, uint32_t cond) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.u64 [%0], %1;\n\t}"
-                 ::"r"(a), "l"(v), "r"(cond) : "memory");
-}
+// Exact 64-bit sums in shared memory kept as two 32-bit words per counter: the
+// low words lo[0..n) and, n words further, the high words.  A value is added
+// to the low word with a native 32-bit atomic; the one addition that wraps the
+// low word sees its old value exceed the new one and adds the carry to the high
+// word.  The pair therefore holds the exact sum (below 2^64) whatever the
+// order of the additions, at the cost of 32-bit atomics only (a 64-bit add to
+// shared memory is not a single instruction).
+struct SFix {
+    uint32_t *lo;  // [2n]: low words, then high words
+    int n;
+    __device__ __forceinline__ void add(int idx, uint32_t v) const {
+        const unsigned a = (unsigned)__cvta_generic_to_shared(lo + idx);
+        const unsigned h = a + 4u * (unsigned)n;
+        asm volatile("{\n\t.reg .pred c;\n\t.reg .u32 o, t;\n\t"
+                     "atom.shared.add.u32 o, [%0], %1;\n\t"
+                     "add.u32 t, o, %1;\n\t"
+                     "setp.lt.u32 c, t, o;\n\t"
+                     "@c red.shared.add.u32 [%2], 1;\n\t}"
+                     ::"r"(a), "r"(v), "r"(h) : "memory");
+    }
+    // add v only where cond != 0 (predicated, no branch)
+    __device__ __forceinline__ void add_if(int idx, uint32_t v, uint32_t cond) const {
+        const unsigned a = (unsigned)__cvta_generic_to_shared(lo + idx);
+        const unsigned h = a + 4u * (unsigned)n;
+        asm volatile("{\n\t.reg .pred q, c;\n\t.reg .u32 o, t;\n\t"
+                     "setp.ne.u32 q, %3, 0;\n\t"
+                     "mov.u32 o, 0;\n\t"
+                     "@q atom.shared.add.u32 o, [%0], %1;\n\t"
+                     "add.u32 t, o, %1;\n\t"
+                     "setp.lt.u32 c, t, o;\n\t"
+                     "and.pred c, c, q;\n\t"
+                     "@c red.shared.add.u32 [%2], 1;\n\t}"
+                     ::"r"(a), "r"(v), "r"(h), "r"(cond) : "memory");
+    }
+    // a 64-bit value (below 2^63): low half with carry, high half added directly
+    __device__ __forceinline__ void add64(int idx, unsigned long long v) const {
+        add(idx, (uint32_t)v);
+        const uint32_t vh = (uint32_t)(v >> 32);
+        if (vh) atomicAdd(lo + n + idx, vh);
+    }
+    __device__ __forceinline__ unsigned long long get(int idx) const {
+        return ((unsigned long long)lo[n + idx] << 32) + lo[idx];
+    }
+    __device__ __forceinline__ void zero(int idx) const {
+        lo[idx] = 0u;
+        lo[n + idx] = 0u;
+    }
+};
 
 // Breakpoint of a knapsack that one item j of the user touches alone:
 // lambda_k + (p~_j - theta_j) / b_jk, always rounded the same way (no
@@ -571,7 +608,7 @@ __device__ __forceinline__ float breakpoint_value(float lamk, float margin, floa
 // the user's k-consumption at lambda^t), and the breakpoints inside the window
 // buffered.
 struct WindowSink {
-    unsigned long long *reg6;  // [3][2][K] (shared): region (above, inside, below the
+    SFix reg6;                 // [3][2][K] (shared): region (above, inside, below the
                                // window) x (v1 > lambda_k^t), knapsack fastest (banks)
     int K;
     const float4 *kinfo;       // [K] (shared): lambda_k (f32), window low, window high (exclusive)
@@ -580,11 +617,10 @@ struct WindowSink {
     int cap_kb, G, blk;
     float bscale;
     // emission of (v1, v2) whose mass m = bmass(v2, bscale) is already known
-    __device__ __forceinline__ void emit_km(int k, const float4 &ki, float v1, float v2,
-                                            unsigned long long m) {
+    __device__ __forceinline__ void emit_km(int k, const float4 &ki, float v1, float v2, uint32_t m) {
         if (!(v1 > 0.f)) return;
         const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-        shared_add_u64(&reg6[(2 * r + (v1 > ki.x ? 1 : 0)) * K + k], m);
+        reg6.add((2 * r + (v1 > ki.x ? 1 : 0)) * K + k, m);
         if (r == 1) {
             const uint32_t slot = shared_inc_u32(&bcnt[k]);
             if (slot < (uint32_t)cap_kb)
@@ -596,15 +632,15 @@ struct WindowSink {
     }
     // bin b = 2 * region + (v1 > lambda_k^t) of a breakpoint with mass m,
     // where emit holds (predicated)
-    __device__ __forceinline__ void region_add_if(int k, int b, unsigned long long m, bool emit) {
-        shared_add_u64_if(&reg6[b * K + k], m, emit ? 1u : 0u);
+    __device__ __forceinline__ void region_add_if(int k, int b, uint32_t m, bool emit) {
+        reg6.add_if(b * K + k, m, emit ? 1u : 0u);
     }
     // predicated emission (pred false: nothing); the buffer append is a rare branch
     __device__ __forceinline__ void emit_if(int k, const float4 &ki, float v1, float v2, bool pred) {
         const bool go = pred && v1 > 0.f && v2 > 0.f;
-        const unsigned long long m = bmass(v2, bscale);
+        const uint32_t m = bmass(v2, bscale);
         const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-        shared_add_u64_if(&reg6[(2 * r + (v1 > ki.x ? 1 : 0)) * K + k], m, go ? 1u : 0u);
+        reg6.add_if((2 * r + (v1 > ki.x ? 1 : 0)) * K + k, m, go ? 1u : 0u);
         if (go && r == 1) buffer_add(k, v1, v2);
     }
     // a breakpoint inside the window whose mass region_add_if took
@@ -633,16 +669,16 @@ struct RefineSink {
         const uint32_t key = key_of(v1);
         if (key < lo[k] || key >= hi[k]) return;
         const int sb = (int)((key - lo[k]) >> shift[k]);
-        atomicAdd(&subhist[(size_t)k * NSUB + sb], bmass(v2, bscale));
+        atomicAdd(&subhist[(size_t)k * NSUB + sb], (unsigned long long)bmass(v2, bscale));
         const uint32_t slot = shared_inc_u32(&bcnt[k]);
         if (slot < (uint32_t)cap_kb)
             buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key, __float_as_uint(v2));
     }
     __device__ __forceinline__ void emit_ki(int k, const float4 &, float v1, float v2) { emit(k, v1, v2); }
-    __device__ __forceinline__ void emit_km(int k, const float4 &, float v1, float v2, unsigned long long) {
+    __device__ __forceinline__ void emit_km(int k, const float4 &, float v1, float v2, uint32_t) {
         emit(k, v1, v2);
     }
-    __device__ __forceinline__ void region_add_if(int, int, unsigned long long, bool) {}
+    __device__ __forceinline__ void region_add_if(int, int, uint32_t, bool) {}
     __device__ __forceinline__ void buffer_add(int, float, float) {}
     __device__ __forceinline__ void emit_if(int k, const float4 &, float v1, float v2, bool pred) {
         if (pred) emit(k, v1, v2);
@@ -652,8 +688,8 @@ struct RefineSink {
 struct NullSink {
     __device__ __forceinline__ void emit(int, float, float) {}
     __device__ __forceinline__ void emit_ki(int, const float4 &, float, float) {}
-    __device__ __forceinline__ void emit_km(int, const float4 &, float, float, unsigned long long) {}
-    __device__ __forceinline__ void region_add_if(int, int, unsigned long long, bool) {}
+    __device__ __forceinline__ void emit_km(int, const float4 &, float, float, uint32_t) {}
+    __device__ __forceinline__ void region_add_if(int, int, uint32_t, bool) {}
     __device__ __forceinline__ void buffer_add(int, float, float) {}
     __device__ __forceinline__ void emit_if(int, const float4 &, float, float, bool) {}
 };

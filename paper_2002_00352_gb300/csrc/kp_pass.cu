@@ -94,12 +94,12 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
     uint32_t *lo = (uint32_t *)(smem + L.lo);
     uint32_t *hi = (uint32_t *)(smem + L.hi);
     int32_t *shift = (int32_t *)(smem + L.shift);
-    unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
+    const SFix rfix{(uint32_t *)(smem + L.rfix), K};
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         float lf = (float)lam[k];
         lamf[k] = lf;
         bcnt[k] = 0;
-        rfix[k] = 0;
+        rfix.zero(k);
         if (MODE == MODE_HIST) {
             SelK sk = S.sel[k];
             const uint32_t lk = lf > 0.f ? __float_as_uint(lf) : 0u;
@@ -118,9 +118,9 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
                 S.sel[k].whi = whi;
             }
             ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, __uint_as_float(wlo), __uint_as_float(whi), 0.f);
-            unsigned long long *r6 = (unsigned long long *)(smem + L.reg3);
+            const SFix r6{(uint32_t *)(smem + L.reg3), 6 * K};
 #pragma unroll
-            for (int q = 0; q < 6; ++q) r6[q * K + k] = 0ull;
+            for (int q = 0; q < 6; ++q) r6.zero(q * K + k);
         } else {
             ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, 0.f, 0.f, 0.f);
         }
@@ -152,10 +152,13 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
     if (blk < 0) blk = blockIdx.x - S.g_lo;
     const int K = P.K;
     uint32_t *bcnt = (uint32_t *)(smem + L.bcnt);
-    unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
+    const SFix rfix{(uint32_t *)(smem + L.rfix), K};
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        if (MODE != MODE_REFINE && rfix[k]) atomicAdd(&S.Rfix[k], rfix[k]);
+        if (MODE != MODE_REFINE) {
+            const unsigned long long r = rfix.get(k);
+            if (r) atomicAdd(&S.Rfix[k], r);
+        }
         if (MODE != MODE_STATE) {
             uint32_t c = bcnt[k];
             S.bufcnt[(size_t)k * S.gspan + blk] = c < (uint32_t)S.cap_kb ? c : (uint32_t)S.cap_kb;
@@ -163,15 +166,15 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
         }
     }
     if (MODE == MODE_HIST) {
-        const unsigned long long *r6 = (const unsigned long long *)(smem + L.reg3);
+        const SFix r6{(uint32_t *)(smem + L.reg3), 6 * K};
         for (int q = threadIdx.x; q < K * 3; q += blockDim.x) {  // q = 3k + r
             const int k = q / 3, r = q - 3 * k;
-            const unsigned long long m = r6[(2 * r) * K + k] + r6[(2 * r + 1) * K + k];
+            const unsigned long long m = r6.get((2 * r) * K + k) + r6.get((2 * r + 1) * K + k);
             if (m) atomicAdd(&S.reg3[q], m);
         }
         if (r_from_bins)
             for (int k = threadIdx.x; k < K; k += blockDim.x) {
-                const unsigned long long m = r6[1 * K + k] + r6[3 * K + k] + r6[5 * K + k];
+                const unsigned long long m = r6.get(1 * K + k) + r6.get(3 * K + k) + r6.get(5 * K + k);
                 if (m) atomicAdd(&S.Rfix[k], m);
             }
     }
@@ -191,7 +194,7 @@ __device__ __forceinline__ void flush_block_state(const Params &P, const Scratch
 __device__ __forceinline__ WindowSink make_window_sink(const Params &P, const Scratch &S,
                                                        const SmemLayout &L, unsigned char *smem) {
     WindowSink ws;
-    ws.reg6 = (unsigned long long *)(smem + L.reg3);
+    ws.reg6 = SFix{(uint32_t *)(smem + L.reg3), 6 * P.K};
     ws.K = P.K;
     ws.kinfo = (const float4 *)(smem + L.kinfo);
     ws.bcnt = (uint32_t *)(smem + L.bcnt);
@@ -266,7 +269,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *s_scan) {
 template <int MAXM, int MODE, class Sink>
 __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t i, int64_t e0,
                                          int nnz, const float *lamf, float *pt, float *mg,
-                                         unsigned long long *rfix, unsigned long long &dsum, unsigned long long &psum,
+                                         const SFix &rfix, unsigned long long &dsum, unsigned long long &psum,
                                          uint32_t *x_bits, Sink &sink) {
     const int M = P.M;
     const Tree &T = P.tree;
@@ -301,8 +304,7 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
             if ((w.sel >> j) & 1ull) {
                 du += pt[j];
                 pu += __ldg(pr + j);
-                for (int q = 0; q < c; ++q)
-                    shared_add_u64(&rfix[kid[e + q]], bmass(__ldg(val + e + q), P.bscale));
+                for (int q = 0; q < c; ++q) rfix.add(kid[e + q], bmass(__ldg(val + e + q), P.bscale));
             }
             e += c;
         }
@@ -415,7 +417,7 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
 template <int MAXM, int C, int MODE, class Sink>
 __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch &S, int64_t i,
                                                   int64_t e0, const float *lamf, const float4 *kinfo,
-                                                  unsigned long long *rfix, unsigned long long &dsum,
+                                                  const SFix &rfix, unsigned long long &dsum,
                                                   unsigned long long &psum, uint32_t *x_bits,
                                                   Sink &sink, float *prow, uint32_t &shared_entries) {
     constexpr int EC = C > 0 ? MAXM * C : 1;
@@ -545,7 +547,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 pu += sj ? __ldg(pr + j) : 0.f;
                 if (!FOLD)
 #pragma unroll
-                    for (int q = 0; q < C; ++q) shared_add_u64_if(&rfix[kk[j * C + q]], bmass(vv[j * C + q], P.bscale), sj);
+                    for (int q = 0; q < C; ++q) rfix.add_if(kk[j * C + q], bmass(vv[j * C + q], P.bscale), sj);
             }
         } else {
             int e = 0;
@@ -554,8 +556,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 if ((G >> j) & 1u) {
                     du += pt[j];
                     pu += __ldg(pr + j);
-                    for (int q = 0; q < cnt[j]; ++q)
-                        shared_add_u64(&rfix[kid[e + q]], bmass(__ldg(val + e + q), P.bscale));
+                    for (int q = 0; q < cnt[j]; ++q) rfix.add(kid[e + q], bmass(__ldg(val + e + q), P.bscale));
                 }
                 e += cnt[j];
             }
@@ -612,7 +613,7 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                 const float v = vv[e];
                 const int k = kk[e];
                 const float4 ki = kinfo[k];
-                const unsigned long long m = bmass(v, P.bscale);
+                const uint32_t m = bmass(v, P.bscale);
                 const float v1 = breakpoint_value(ki.x, mg[j], v);
                 const bool emit = v > 0.f && v1 > 0.f && !((shm.x >> e) & 1u);
                 const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
@@ -790,7 +791,7 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
     const int M = P.M;
     const float *lamf = (const float *)(smem + L.lamf);
     const float4 *kinfo = (const float4 *)(smem + L.kinfo);
-    unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
+    const SFix rfix{(uint32_t *)(smem + L.rfix), P.K};
     float *rows = (float *)(smem + L.rows);
     if constexpr (C > 0 && MODE != MODE_STATE && MAXM <= 16) if (sets == CSR_SETS) {
         // regular rows: CSR_SETS consecutive tiles of users per sweep phase, so
@@ -1026,7 +1027,7 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
                                            unsigned long long &psum) {
     const int M = P.M, K = P.K;
     const float *lamf = (const float *)(smem + L.lamf);
-    unsigned long long *rfix = (unsigned long long *)(smem + L.rfix);
+    const SFix rfix{(uint32_t *)(smem + L.rfix), K};
     float *tp = (float *)(smem + L.tile_p);
     float *tb = (float *)(smem + L.tile_b);
     float *pt = (float *)(smem + L.rows);
@@ -1112,7 +1113,7 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
                 r &= r - 1;
                 acc += bmass(bcol[(size_t)j * K], P.bscale);
             }
-            if (acc) shared_add_u64(&rfix[k], acc);
+            if (acc) rfix.add64(k, acc);
         }
         if (MODE != MODE_STATE) {
             uint64_t J = 0;

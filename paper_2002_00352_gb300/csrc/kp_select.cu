@@ -118,7 +118,7 @@ __device__ uint32_t exact_select(const Scratch &S, const Params &P, int k, uint3
             for (uint32_t s = threadIdx.x; s < cnt; s += blockDim.x) {
                 const uint2 e = base[s];
                 const uint32_t off = e.x - clo;
-                if (e.x >= clo && off < width) atomicAdd(&h[off >> sh], bmass(__uint_as_float(e.y), P.bscale));
+                if (e.x >= clo && off < width) atomicAdd(&h[off >> sh], (unsigned long long)bmass(__uint_as_float(e.y), P.bscale));
             }
         }
         __syncthreads();
