@@ -32,13 +32,22 @@ namespace kp {
 namespace {
 
 constexpr int DENSE_TILE_BYTES = 64 * 1024;   // dense b tile
-constexpr int CSR_SETS = 3;                    // CSR user tiles per sweep phase (regular rows)
 
 struct SmemLayout {
     size_t lamf, kinfo, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Per-warp queue of pair sweeps (regular CSR rows): a ring of WQ_OWN owners
+// (p~ row, rank masks, user index) and a ring of WQ_TASKS tasks (owner slot,
+// first and second entry).  After each round of users fewer than 32 tasks
+// wait, so at most 31 + 32 owners and 31 + 96 tasks are ever held.
+constexpr int WQ_OWN = 64;
+constexpr int WQ_TASKS = 128;
+__host__ __device__ inline size_t wq_bytes(int maxm) {
+    return align16((size_t)WQ_OWN * (8 * (size_t)maxm + 8) + (size_t)WQ_TASKS * 2);
+}
 
 __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int maxm, int threads,
                                                   int T, int mode, int sets = 1) {
@@ -64,9 +73,11 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
     s.red = o;
     o = align16(o + 2 * 8 * 32);
     if (layout == KP_B_CSR) {
-        s.rows = o;  // per thread: p~ row and rank masks (for shared-knapsack sweeps)
-        // (rows of the register path only: M <= 16; `sets` sets of them)
-        if (mode != MODE_STATE && maxm <= 16) o = align16(o + (size_t)sets * 2 * 4 * (size_t)threads * maxm);
+        s.rows = o;  // pair-sweep owners' p~ rows and rank masks (register path only: M <= 16):
+        // per thread (irregular rows), or per warp a ring of WQ_OWN owners and a
+        // ring of WQ_TASKS tasks (regular rows, sets == 0)
+        if (mode != MODE_STATE && maxm <= 16)
+            o = align16(o + (sets == 0 ? (size_t)(threads / 32) * wq_bytes(maxm) : 2 * 4 * (size_t)threads * maxm));
         s.tile_p = s.tile_b = s.selm = o;
     } else {
         s.tile_p = o;
@@ -83,6 +94,22 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
 }
 
 __device__ __forceinline__ int bitlen(uint32_t x) { return x ? 32 - __clz(x) : 0; }
+
+// Relevance bound of a knapsack (kinfo.w).  A pass needs only the breakpoints
+// at or above a floor: in the breakpoint pass of regular CSR rows,
+// min(window low, lambda_k^t) (nothing below both is read); in a re-run pass,
+// the low end of the unresolved range (+inf when resolved).  A breakpoint
+// lambda_k + m / b lies below the floor whenever m < t * b with
+//   t = floor - lambda_k - (2^-8 |floor - lambda_k| + 2^-18 (|lambda_k| + |floor|)),
+// the margin covering the FP32 rounding of the breakpoint, so such entries are
+// skipped without computing them.  Every event of a line is at or below its
+// zero crossing lambda_k + p~ / b (the sweeps clamp each event to the
+// previous one, the first to a zero crossing or a crossing with a weaker
+// selected line), so the same bound with p~ for m skips a whole sweep.
+__device__ __forceinline__ float low_bound(float floor_v, float lamk) {
+    const float d = floor_v - lamk;
+    return d - (0x1p-8f * fabsf(d) + 0x1p-18f * (fabsf(lamk) + fabsf(floor_v)) + 1e-30f);
+}
 
 template <int MODE>
 __device__ __forceinline__ void init_block_state(const Params &P, const Scratch &S,
@@ -117,12 +144,18 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
                 S.sel[k].wlo = wlo;
                 S.sel[k].whi = whi;
             }
-            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, __uint_as_float(wlo), __uint_as_float(whi), 0.f);
+            ((float4 *)(smem + L.kinfo))[k] =
+                make_float4(lf, __uint_as_float(wlo), __uint_as_float(whi), low_bound(fminf(__uint_as_float(wlo), lf), lf));
             const SFix r6{(uint32_t *)(smem + L.reg3), 6 * K};
 #pragma unroll
             for (int q = 0; q < 6; ++q) r6.zero(q * K + k);
         } else {
-            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, 0.f, 0.f, 0.f);
+            float t = 0.f;
+            if (MODE == MODE_REFINE) {
+                const SelK sk = S.sel[k];
+                t = sk.state == 1 ? low_bound(__uint_as_float(sk.lo), lf) : __int_as_float(0x7f800000);
+            }
+            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, 0.f, 0.f, t);
         }
         if (MODE == MODE_REFINE) {
             SelK sk = S.sel[k];
@@ -419,7 +452,9 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                                                   int64_t e0, const float *lamf, const float4 *kinfo,
                                                   const SFix &rfix, unsigned long long &dsum,
                                                   unsigned long long &psum, uint32_t *x_bits,
-                                                  Sink &sink, float *prow, uint32_t &shared_entries) {
+                                                  Sink &sink, float *prow, uint32_t &shared_entries,
+                                                  unsigned wmask, float *orow = nullptr, uint32_t *obeat = nullptr,
+                                                  unsigned otail = 0u) {
     constexpr int EC = C > 0 ? MAXM * C : 1;
     // breakpoint pass with every entry in registers: the consumption of the
     // selected items is taken in the same predicated loop as the breakpoints
@@ -598,39 +633,59 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) mg[j] = pt[j] - (((G >> j) & 1u) ? ts[j] : tn[j]);
         const uint2 shm = S.shmask[i];
-        const uint32_t pending = shm.y;
+        uint32_t pending = shm.y;
         shared_entries = shm.x;
         if constexpr (FOLD) {
-            // Algorithm 4 Map, closed form for knapsacks only one item touches:
-            // one predicated pass over the entries in registers; breakpoints
-            // that fall inside the window are buffered afterwards.  The
-            // consumption at lambda^t is not summed here: it is the mass of
-            // the breakpoints above lambda_k^t (flush_block_state).
-            uint32_t inside = 0u;
+            // Algorithm 4 Map, closed form for knapsacks only one item touches.
+            // A cheap first pass marks the entries whose breakpoint can reach a
+            // bin the selection reads (m >= t_k b, see low_bound) and the pair
+            // entries whose line's zero crossing can (p~ >= t_k b); only the
+            // marked entries get the breakpoint, its bin and, inside the
+            // window, the buffer.  The consumption at lambda^t is not summed
+            // here: it is the mass of the breakpoints above lambda_k^t
+            // (flush_block_state), all of them marked (t_k <= 0 < m).
+            uint32_t rel = 0u, zrel = 0u;
+            float mgl[MAXM];
+#pragma unroll
+            for (int j = 0; j < MAXM; ++j) mgl[j] = mg[j];
 #pragma unroll
             for (int e = 0; e < EC; ++e) {
                 const int j = e / C;
                 const float v = vv[e];
-                const int k = kk[e];
-                const float4 ki = kinfo[k];
-                const uint32_t m = bmass(v, P.bscale);
-                const float v1 = breakpoint_value(ki.x, mg[j], v);
-                const bool emit = v > 0.f && v1 > 0.f && !((shm.x >> e) & 1u);
-                const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
-                // breakpoints below both the window and lambda_k^t add to no
-                // mass the selection reads (the select then learns whether
-                // everything fits from a re-run over the range below)
-                const bool above_t = v1 > ki.x;
-                sink.region_add_if(k, 2 * r + (above_t ? 1 : 0), m, emit && (r != 2 || above_t));
-                inside |= (emit && r == 1) ? 1u << e : 0u;
+                const float tv = kinfo[kk[e]].w * v;
+                const bool live = v > 0.f;
+                rel |= (live && !((shm.x >> e) & 1u) && mg[j] >= tv) ? 1u << e : 0u;
+                zrel |= (live && pt[j] >= tv) ? 1u << e : 0u;
             }
-            while (inside) {
-                const int e = __ffs(inside) - 1;
-                inside &= inside - 1;
+            while (rel) {
+                const int e = __ffs(rel) - 1;
+                rel &= rel - 1;
                 const int k = kid[e];
                 const float v = __ldg(val + e);
-                sink.buffer_add(k, breakpoint_value(kinfo[k].x, pick(mg, e / C), v), v);
+                const float4 ki = kinfo[k];
+                const float v1 = breakpoint_value(ki.x, mgl[e / C], v);
+                const bool emit = v1 > 0.f;
+                const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
+                const bool above_t = v1 > ki.x;
+                sink.region_add_if(k, 2 * r + (above_t ? 1 : 0), bmass(v, P.bscale), emit && (r != 2 || above_t));
+                if (emit && r == 1) sink.buffer_add(k, v1, v);
             }
+            // the lanes leave the loop above after different trip counts: meet
+            // again before the rest of the user's work (otherwise the warp may
+            // run it, and the next users, once per group of lanes)
+            __syncwarp(wmask);
+            // pairs whose two lines both cross zero below the floor add nothing
+            uint32_t kept = 0u;
+            int nk = 0;
+            for (int t = 0; t < pair_count(pending); ++t) {
+                const int e = pair_first(pending, t), e2 = pair_second(pending, t);
+                if (((zrel >> e) | (zrel >> e2)) & 1u) {
+                    kept |= (uint32_t)((e | (e2 << 5)) << (10 * nk));
+                    ++nk;
+                }
+            }
+            pending = nk ? (kept | ((uint32_t)nk << 30)) : 0u;
+            __syncwarp(wmask);
         } else {
             // Algorithm 4 Map: closed form for knapsacks only one item touches.
             // One rolled copy of the emission body keeps the code in the
@@ -647,13 +702,23 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
                     const float v = __ldg(val + e);
                     if (v > 0.f) {
                         const float4 ki = kinfo[k];
+                        // a re-run pass skips breakpoints below its range (low_bound)
+                        if (MODE == MODE_REFINE && !(m >= ki.w * v)) continue;
                         sink.emit_ki(k, ki, breakpoint_value(ki.x, m, v), v);
                     }
                 }
             }
         }
+        uint32_t *brow = nullptr;
+        if (orow) {  // the warp's owner ring: slot otail + rank among the lanes with pairs
+            const unsigned ob = __ballot_sync(wmask, pending != 0u);
+            const unsigned slot = (otail + __popc(ob & ((1u << (threadIdx.x & 31)) - 1u))) & (WQ_OWN - 1);
+            prow = orow + slot * MAXM;
+            brow = obeat + slot * MAXM;
+        } else if (pending) {
+            brow = reinterpret_cast<uint32_t *>(prow + (size_t)blockDim.x * MAXM);
+        }
         if (pending) {
-            uint32_t *brow = reinterpret_cast<uint32_t *>(prow + (size_t)blockDim.x * MAXM);
 #pragma unroll
             for (int j = 0; j < MAXM; ++j) {
                 prow[j] = pt[j];
@@ -793,33 +858,62 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
     const float4 *kinfo = (const float4 *)(smem + L.kinfo);
     const SFix rfix{(uint32_t *)(smem + L.rfix), P.K};
     float *rows = (float *)(smem + L.rows);
-    if constexpr (C > 0 && MODE != MODE_STATE && MAXM <= 16) if (sets == CSR_SETS) {
-        // regular rows: CSR_SETS consecutive tiles of users per sweep phase, so
-        // the block meets its barriers once per CSR_SETS tiles (when the rows of
-        // CSR_SETS tiles fit in shared memory next to the per-knapsack state)
-        constexpr int U = CSR_SETS;
-        constexpr size_t SET = 2 * (size_t)THREADS * MAXM;
-        const int64_t step = (int64_t)gridDim.x * THREADS * U;
-        for (int64_t base = (int64_t)blockIdx.x * THREADS * U; base < P.N; base += step) {
-            int64_t ee[U];
-            uint32_t pend[U];
-#pragma unroll 1
-            for (int u = 0; u < U; ++u) {
-                const int64_t i = base + (int64_t)u * THREADS + threadIdx.x;
-                const int64_t e0 = P.uoff0 + i * (int64_t)(M * C);
-                uint32_t pd = 0u, shm = 0u;
-                if (i < P.N)
-                    pd = csr_user_fast<MAXM, C, MODE>(P, S, i, e0, lamf, kinfo, rfix, dsum, psum, x_bits, sink,
-                                                      rows + u * SET + (size_t)threadIdx.x * MAXM, shm);
-#pragma unroll
-                for (int v = 0; v < U; ++v)
-                    if (v == u) {
-                        ee[v] = e0;
-                        pend[v] = pd;
-                    }
+    if constexpr (C > 0 && MODE != MODE_STATE && MAXM <= 16) if (sets == 0) {
+        // regular rows: each warp queues its users' pair sweeps and sweeps 32 of
+        // them at a time, so the loop has no block barrier and every sweep round
+        // is full
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        unsigned char *wq = smem + L.rows + (size_t)warp * wq_bytes(MAXM);
+        float *orow = (float *)wq;                                      // [WQ_OWN][MAXM]
+        uint32_t *obeat = (uint32_t *)(orow + WQ_OWN * MAXM);            // [WQ_OWN][MAXM]
+        long long *ouser = (long long *)(obeat + WQ_OWN * MAXM);         // [WQ_OWN]
+        uint16_t *tq = (uint16_t *)(ouser + WQ_OWN);                     // [WQ_TASKS]
+        unsigned head = 0u, tail = 0u, otail = 0u;                       // the same in every lane
+        const unsigned lt = (1u << lane) - 1u;
+        auto round = [&](int ntask) {
+            if (lane < ntask) {
+                const uint32_t d = tq[(head + lane) & (WQ_TASKS - 1)];
+                const int slot = (int)(d >> 10);
+                const int64_t oi = ouser[slot];
+                sweep_task<MAXM, C>(P, kinfo, orow + slot * MAXM, obeat + slot * MAXM, oi,
+                                    P.uoff0 + oi * (int64_t)(M * C), (int)(d & 31u), (int)((d >> 5) & 31u), sink);
             }
-            block_sweeps<MAXM, C, THREADS, U>(P, kinfo, rows, base, ee, pend, sink);
+            __syncwarp();
+        };
+        for (int64_t base = (int64_t)blockIdx.x * THREADS; base < P.N; base += (int64_t)gridDim.x * THREADS) {
+            const int64_t i = base + threadIdx.x;
+            const int64_t e0 = P.uoff0 + i * (int64_t)(M * C);
+            uint32_t pd = 0u, shm = 0u;
+            const unsigned wmask = __ballot_sync(0xffffffffu, i < P.N);  // lanes that run a user
+            if (i < P.N)
+                pd = csr_user_fast<MAXM, C, MODE>(P, S, i, e0, lamf, kinfo, rfix, dsum, psum, x_bits, sink,
+                                                  nullptr, shm, wmask, orow, obeat, otail);
+            // enqueue the user's pairs; its row was written to owner slot otail + rank
+            const unsigned ob = __ballot_sync(0xffffffffu, pd != 0u);
+            const int n = pair_count(pd);
+            int x = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, x, 31);
+            if (pd) {
+                const unsigned slot = (otail + __popc(ob & lt)) & (WQ_OWN - 1);
+                ouser[slot] = i;
+                for (int t = 0; t < n; ++t)
+                    tq[(tail + (unsigned)(x - n + t)) & (WQ_TASKS - 1)] =
+                        (uint16_t)((slot << 10) | (unsigned)pair_first(pd, t) | ((unsigned)pair_second(pd, t) << 5));
+            }
+            tail += (unsigned)total;
+            otail += (unsigned)__popc(ob);
+            __syncwarp();
+            while (tail - head >= 32u) {
+                round(32);
+                head += 32u;
+            }
         }
+        if (tail != head) round((int)(tail - head));
         return;
     }
     for (int64_t base = (int64_t)blockIdx.x * THREADS; base < P.N; base += (int64_t)gridDim.x * THREADS) {
@@ -841,12 +935,13 @@ __device__ __forceinline__ void csr_loop(const Params &P, const Scratch &S, unsi
             e0 = s_base + excl;
         }
         uint32_t pending = 0u, shm = 0u;
+        const unsigned wmask = __ballot_sync(0xffffffffu, valid && nnz <= 32);  // lanes of the register path
         if (valid) {
             bool done = false;
             if constexpr (MAXM <= 16) {
                 if (nnz <= 32) {
                     pending = csr_user_fast<MAXM, C, MODE>(P, S, i, e0, lamf, kinfo, rfix, dsum, psum, x_bits,
-                                                           sink, rows + (size_t)threadIdx.x * MAXM, shm);
+                                                           sink, rows + (size_t)threadIdx.x * MAXM, shm, wmask);
                     done = true;
                 }
             }
@@ -958,6 +1053,13 @@ __device__ __forceinline__ void rare_task(const Params &P, const float4 *kinfo, 
                 if (((inl >> j) & 1u) && __popc(bt[j] & inl) >= cap) drop |= 1u << j;
             SF &= ~drop;
         }
+        // every event lies at or below a moving line's zero crossing: nothing
+        // to emit when all of them lie below the pass's floor (low_bound)
+        const float tk = kinfo[k].w;
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < XMAX; ++q) any |= q < nj && pick(w, it[q]) >= tk * sl[q];
+        if (nj <= XMAX && !any) return;
         if (nj <= XMAX) {
             exchange_sweep<XMAX, MAXM>(w, SF, nj, it, sl, kinfo[k].x, T, k, sink);
             return;
@@ -1232,10 +1334,11 @@ cudaError_t launch_csr(const Params &P, const Scratch &S, const double *lam, uin
     static int max_dyn = -1;  // once per instantiation, before any stream capture
     cudaError_t e = prepare_kernel(kern, &max_dyn);
     if (e != cudaSuccess) return e;
-    // CSR_SETS tiles per sweep phase when their rows fit, else one
-    int sets = (C > 0 && MODE != MODE_STATE && MAXM <= 16) ? CSR_SETS : 1;
+    // regular rows: per-warp pair queues (sets = 0) when they fit next to the
+    // per-knapsack state, else per-thread rows swept after every tile
+    int sets = (C > 0 && MODE != MODE_STATE && MAXM <= 16) ? 0 : 1;
     SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE, sets);
-    if (L.total > (size_t)max_dyn && sets > 1) {
+    if (L.total > (size_t)max_dyn && sets != 1) {
         sets = 1;
         L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE, sets);
     }
