@@ -419,6 +419,97 @@ __device__ __forceinline__ void exchange_sweep(const float (&w)[MAXM], uint32_t 
     }
 }
 
+// Map of Algorithm 4 for one (user, k) over the live moving lines only, in
+// exchange form, for rows of up to 64 items (dense b).  The live lines (slots
+// q < nj, in item order: item it[q], slope sl[q] = b_jk > 0) are the moving
+// lines whose zero crossing can reach the pass's floor; any other moving line
+// stays negative, hence unselected, at every lambda_k at or above the floor,
+// so the events at or above the floor are those of the full sweep, with the
+// same arithmetic whatever the floor (every pass computes identical keys).
+// SF = the greedy selection among the fixed lines (b_jk = 0), w = the user's
+// p~ row.  A line outside S enters when it overtakes the weakest member of its
+// circuit in S (the selected items of the deepest full set on its path: the
+// weakest fixed line, or a selected moving line with a smaller slope) or, with
+// no full set on its path, at its zero crossing; fixed lines never re-enter
+// and a moving line leaves only when overtaken, so the events are few (the
+// loop bound is a guard).  Each event emits (lambda_k, consumption increase).
+template <int MAXM, class Sink>
+__device__ void live_sweep(const float *w, uint64_t SF, int nj, const int *it, const float *sl, float lamk,
+                           const Tree &t, int k, Sink &sink) {
+    float A[MAXM];
+    uint64_t Jm = 0ull, live = 0ull, inq = 0ull;  // items of the live lines; slot masks
+    for (int q = 0; q < nj; ++q) {
+        A[q] = fmaf(lamk, sl[q], w[it[q]]);
+        Jm |= 1ull << it[q];
+        if (A[q] > 0.f) live |= 1ull << q;
+    }
+    uint64_t S = SF;
+    float cur = FLT_MAX;
+    const int guard = 8 * nj * nj + 8;
+    for (int iter = 0; iter < guard && (live & ~inq); ++iter) {
+        uint32_t full = 0u;
+        for (int l = 0; l < t.L; ++l)
+            if (__popcll(S & t.items[l]) >= (int)t.cap[l]) full |= 1u << l;
+        float be = 0.f, bv2 = 0.f;
+        int bq = -1;
+        uint64_t brem = 0ull, bout = 0ull;
+        uint64_t cand = live & ~inq;
+        while (cand) {
+            const int q = __ffsll((long long)cand) - 1;
+            cand &= cand - 1;
+            const uint32_t fm = t.ipath[it[q]] & full;
+            float e, v2 = sl[q];
+            uint64_t rem = 0ull, outq = 0ull;
+            if (!fm) {
+                e = __fdividef(A[q], sl[q]);  // zero crossing, nothing to replace
+            } else {
+                const uint64_t Cm = S & t.items[__ffs(fm) - 1];
+                uint64_t CF = Cm & ~Jm;
+                float wmin = FLT_MAX;  // weakest fixed member (ties: the higher index is weaker)
+                uint64_t yb = 0ull;
+                while (CF) {
+                    const int j = __ffsll((long long)CF) - 1;
+                    CF &= CF - 1;
+                    const float v = w[j];
+                    if (v <= wmin) {
+                        wmin = v;
+                        yb = 1ull << j;
+                    }
+                }
+                e = yb ? __fdividef(A[q] - wmin, sl[q]) : -1.f;
+                rem = yb;
+                uint64_t mv = inq;  // selected moving members with a smaller slope
+                while (mv) {
+                    const int r = __ffsll((long long)mv) - 1;
+                    mv &= mv - 1;
+                    if (((Cm >> it[r]) & 1ull) && sl[q] > sl[r]) {
+                        const float x = __fdividef(A[q] - A[r], sl[q] - sl[r]);
+                        if (x > e) {
+                            e = x;
+                            rem = 1ull << it[r];
+                            outq = 1ull << r;
+                            v2 = sl[q] - sl[r];
+                        }
+                    }
+                }
+            }
+            if (e > cur) e = cur;
+            if (e > be) {
+                be = e;
+                bq = q;
+                brem = rem;
+                bout = outq;
+                bv2 = v2;
+            }
+        }
+        if (bq < 0) break;
+        S = (S & ~brem) | (1ull << it[bq]);
+        inq = (inq & ~bout) | (1ull << bq);
+        cur = be;
+        sink.emit_rel(k, be, bv2);
+    }
+}
+
 // Sets whose count reached their cap in the selection S.
 __device__ __forceinline__ uint32_t full_sets(uint32_t S, const Tree &t) {
     uint32_t full = 0u;
@@ -653,6 +744,16 @@ struct WindowSink {
         if (!(v2 > 0.f)) return;
         emit_ki(k, kinfo[k], v1, v2);
     }
+    // emission of the dense breakpoint pass: only the window and above are
+    // binned (the bins below the window hold each user's total mass instead)
+    __device__ __forceinline__ void emit_rel(int k, float v1, float v2) {
+        if (!(v1 > 0.f) || !(v2 > 0.f)) return;
+        const float4 ki = kinfo[k];
+        const int r = v1 >= ki.z ? 0 : (v1 >= ki.y ? 1 : 2);
+        if (r == 2) return;
+        reg6.add((2 * r) * K + k, bmass(v2, bscale));
+        if (r == 1) buffer_add(k, v1, v2);
+    }
 };
 
 // Refine pass: sub-histogram of the unresolved range + buffer of its entries.
@@ -675,6 +776,7 @@ struct RefineSink {
             buf[((size_t)k * G + blk) * cap_kb + slot] = make_uint2(key, __float_as_uint(v2));
     }
     __device__ __forceinline__ void emit_ki(int k, const float4 &, float v1, float v2) { emit(k, v1, v2); }
+    __device__ __forceinline__ void emit_rel(int k, float v1, float v2) { emit(k, v1, v2); }
     __device__ __forceinline__ void emit_km(int k, const float4 &, float v1, float v2, uint32_t) {
         emit(k, v1, v2);
     }
@@ -687,6 +789,7 @@ struct RefineSink {
 
 struct NullSink {
     __device__ __forceinline__ void emit(int, float, float) {}
+    __device__ __forceinline__ void emit_rel(int, float, float) {}
     __device__ __forceinline__ void emit_ki(int, const float4 &, float, float) {}
     __device__ __forceinline__ void emit_km(int, const float4 &, float, float, uint32_t) {}
     __device__ __forceinline__ void region_add_if(int, int, uint32_t, bool) {}

@@ -144,8 +144,12 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
                 S.sel[k].wlo = wlo;
                 S.sel[k].whi = whi;
             }
-            ((float4 *)(smem + L.kinfo))[k] =
-                make_float4(lf, __uint_as_float(wlo), __uint_as_float(whi), low_bound(fminf(__uint_as_float(wlo), lf), lf));
+            // floor: dense rows read only the window and above (their consumption
+            // comes from x, their total from an evaluation at lambda_k = 0);
+            // regular CSR rows also need the breakpoints above lambda_k^t
+            const float wlf = __uint_as_float(wlo);
+            const float fl = P.layout == KP_B_DENSE ? wlf : fminf(wlf, lf);
+            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, wlf, __uint_as_float(whi), low_bound(fl, lf));
             const SFix r6{(uint32_t *)(smem + L.reg3), 6 * K};
 #pragma unroll
             for (int q = 0; q < 6; ++q) r6.zero(q * K + k);
@@ -1216,17 +1220,69 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
                 acc += bmass(bcol[(size_t)j * K], P.bscale);
             }
             if (acc) rfix.add64(k, acc);
+            if (MODE == MODE_HIST) {
+                // the user's whole emitted mass, its k-consumption as lambda_k -> 0+
+                // (Algorithm 1 at lambda_k = 0; at lambda_k^t = 0 the consumption
+                // above): the selection reads it to decide lambda_k = 0, so the
+                // sweep needs only the lines that reach the window
+                const float lamk = lamf[k];
+                unsigned long long tot = acc;
+                if (lamk > 0.f) {
+                    const float *ptu = pt + (size_t)u * M;
+                    float z[MAXM];
+                    uint64_t zpos = 0ull;
+                    for (int j = 0; j < M; ++j) {
+                        z[j] = fmaf(lamk, bcol[(size_t)j * K], ptu[j]);
+                        if (z[j] > 0.f) zpos |= 1ull << j;
+                    }
+                    Walk w0;
+                    greedy_walk(z, 1, zpos, P.tree, w0);
+                    tot = 0ull;
+                    uint64_t r0 = w0.sel;
+                    while (r0) {
+                        const int j = __ffsll((long long)r0) - 1;
+                        r0 &= r0 - 1;
+                        tot += bmass(bcol[(size_t)j * K], P.bscale);
+                    }
+                }
+                if (tot) SFix{(uint32_t *)(smem + L.reg3), 6 * K}.add64(4 * K + k, tot);  // bin (below, 0)
+            }
         }
         if (MODE != MODE_STATE) {
-            uint64_t J = 0;
-            for (int j = 0; j < M; ++j)
-                if (bcol[(size_t)j * K] > 0.f) J |= 1ull << j;
-            if (MODE == MODE_HIST) {
-                WindowSink ws = make_window_sink(P, S, L, smem);
-                sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, ws);
-            } else {
-                RefineSink rs = make_refine_sink(P, S, L, smem);
-                sweep_k<MAXM>(pt + (size_t)u * M, 1, bcol, K, M, J, lamf[k], P.tree, k, rs);
+            // the moving lines whose zero crossing can reach the pass's floor
+            // (low_bound, kinfo.w); the others never enter at or above it
+            const float *ptu = pt + (size_t)u * M;
+            const float tk = ((const float4 *)(smem + L.kinfo))[k].w;
+            int it[MAXM];
+            float sl[MAXM];
+            int nj = 0;
+            uint64_t fixedpos = 0ull;
+            for (int j = 0; j < M; ++j) {
+                const float b = bcol[(size_t)j * K];
+                const float wj = ptu[j];
+                if (b > 0.f) {
+                    if (wj >= tk * b) {
+                        it[nj] = j;
+                        sl[nj] = b;
+                        ++nj;
+                    }
+                } else if (wj > 0.f) {
+                    fixedpos |= 1ull << j;
+                }
+            }
+            if (nj > 0) {
+                auto run = [&](auto &sink) {
+                    Walk wf;
+                    greedy_walk(ptu, 1, fixedpos, P.tree, wf);  // selection among the fixed lines
+                    live_sweep<MAXM>(ptu, wf.sel, nj, it, sl, lamf[k], P.tree, k, sink);
+                };
+                if (MODE == MODE_HIST) {
+                    WindowSink ws = make_window_sink(P, S, L, smem);
+                    run(ws);
+                } else {
+                    RefineSink rs = make_refine_sink(P, S, L, smem);
+                    run(rs);
+                }
             }
         }
     }

@@ -211,10 +211,14 @@ __device__ __forceinline__ void select_body(const Params &P, Scratch &S, int k, 
             S.reg3[3 * k + 1] = 0ull;
             S.reg3[3 * k + 2] = 0ull;
         }
-        // the regular-CSR breakpoint pass leaves out of Bl the breakpoints
-        // below both the window and lambda_k^t: the total is then unknown here
-        const bool below_known = !(P.layout == KP_B_CSR && P.creg > 0 && P.M <= 16);
-        const unsigned long long total = A + W + Bl;
+        // dense rows: Bl is the total mass (every user's consumption as
+        // lambda_k -> 0+).  Regular CSR rows leave out of Bl the breakpoints
+        // below both the window and lambda_k^t: the total is then known only
+        // when there are none (lambda_k^t = 0, every breakpoint lies above it).
+        const bool dense = P.layout == KP_B_DENSE;
+        const bool skips_low = P.layout == KP_B_CSR && P.creg > 0 && P.M <= 16;
+        const bool below_known = dense || !skips_low || !(lam_t > 0.f);
+        const unsigned long long total = dense ? Bl : A + W + Bl;
         if (below_known && total <= Bfix) {  // the whole mass fits: lambda_k = 0
             if (threadIdx.x == 0) {
                 resolved(sk, k, 0u, lam_t, lam_next);
