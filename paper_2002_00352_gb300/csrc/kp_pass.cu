@@ -1207,10 +1207,38 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
         }
     }
     __syncthreads();
-    // per (user, knapsack): consumption and Algorithm 4's Map
-    for (int idx = threadIdx.x; idx < nu * K; idx += THREADS) {
-        const int u = idx / K, k = idx - u * K;
+    // per (user, knapsack): consumption and Algorithm 4's Map; thread t takes
+    // the tasks t, t + THREADS, ... of the tile (task = u K + k, stepped without
+    // division)
+    const int du = THREADS / K, dk = THREADS - du * K;
+    int u = threadIdx.x / K, k = threadIdx.x - u * K;
+    const float4 *kinfo = (const float4 *)(smem + L.kinfo);
+    // every lane takes the same number of rounds (the tasks' loops have
+    // data-dependent trip counts: the warp meets again after each task)
+    for (int base = 0; base < nu * K; base += THREADS, u += du, k += dk) {
+        if (k >= K) {
+            k -= K;
+            ++u;
+        }
+        if (u < nu) {
         const float *bcol = tb + (size_t)u * M * K + k;
+        const float *ptu = pt + (size_t)u * M;
+        const float lamk = lamf[k];
+        const float tk = MODE == MODE_STATE ? 0.f : kinfo[k].w;
+        // one pass over the items: lines positive at lambda_k = 0, live moving
+        // lines (zero crossing can reach the pass's floor, see low_bound; the
+        // others never enter at or above it), positive fixed lines
+        uint64_t zpos = 0ull, livem = 0ull, fixedpos = 0ull;
+        for (int j = 0; j < M; ++j) {
+            const float b = bcol[(size_t)j * K];
+            const float wj = ptu[j];
+            if (fmaf(lamk, b, wj) > 0.f) zpos |= 1ull << j;
+            if (b > 0.f) {
+                if (wj >= tk * b) livem |= 1ull << j;
+            } else if (wj > 0.f) {
+                fixedpos |= 1ull << j;
+            }
+        }
         if (MODE != MODE_REFINE) {
             uint64_t r = selm[u];
             unsigned long long acc = 0ull;
@@ -1225,72 +1253,64 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
                 // (Algorithm 1 at lambda_k = 0; at lambda_k^t = 0 the consumption
                 // above): the selection reads it to decide lambda_k = 0, so the
                 // sweep needs only the lines that reach the window
-                const float lamk = lamf[k];
                 unsigned long long tot = acc;
                 if (lamk > 0.f) {
-                    const float *ptu = pt + (size_t)u * M;
-                    float z[MAXM];
-                    uint64_t zpos = 0ull;
-                    for (int j = 0; j < M; ++j) {
-                        z[j] = fmaf(lamk, bcol[(size_t)j * K], ptu[j]);
-                        if (z[j] > 0.f) zpos |= 1ull << j;
-                    }
-                    Walk w0;
-                    greedy_walk(z, 1, zpos, P.tree, w0);
                     tot = 0ull;
-                    uint64_t r0 = w0.sel;
-                    while (r0) {
-                        const int j = __ffsll((long long)r0) - 1;
-                        r0 &= r0 - 1;
-                        tot += bmass(bcol[(size_t)j * K], P.bscale);
+                    if (zpos) {
+                        float z[MAXM];
+                        uint64_t q = zpos;
+                        while (q) {
+                            const int j = __ffsll((long long)q) - 1;
+                            q &= q - 1;
+                            z[j] = fmaf(lamk, bcol[(size_t)j * K], ptu[j]);
+                        }
+                        Walk w0;
+                        greedy_walk(z, 1, zpos, P.tree, w0);
+                        uint64_t r0 = w0.sel;
+                        while (r0) {
+                            const int j = __ffsll((long long)r0) - 1;
+                            r0 &= r0 - 1;
+                            tot += bmass(bcol[(size_t)j * K], P.bscale);
+                        }
                     }
                 }
                 if (tot) SFix{(uint32_t *)(smem + L.reg3), 6 * K}.add64(4 * K + k, tot);  // bin (below, 0)
             }
         }
-        if (MODE != MODE_STATE) {
-            // the moving lines whose zero crossing can reach the pass's floor
-            // (low_bound, kinfo.w); the others never enter at or above it
-            const float *ptu = pt + (size_t)u * M;
-            const float tk = ((const float4 *)(smem + L.kinfo))[k].w;
+        if (MODE != MODE_STATE && livem) {
+            const int nj = __popcll(livem);
             int it[MAXM];
             float sl[MAXM];
-            int nj = 0;
-            uint64_t fixedpos = 0ull;
-            for (int j = 0; j < M; ++j) {
-                const float b = bcol[(size_t)j * K];
-                const float wj = ptu[j];
-                if (b > 0.f) {
-                    if (wj >= tk * b) {
-                        it[nj] = j;
-                        sl[nj] = b;
-                        ++nj;
-                    }
-                } else if (wj > 0.f) {
-                    fixedpos |= 1ull << j;
-                }
+            int n = 0;
+            uint64_t q = livem;
+            while (q) {
+                const int j = __ffsll((long long)q) - 1;
+                q &= q - 1;
+                it[n] = j;
+                sl[n] = bcol[(size_t)j * K];
+                ++n;
             }
-            if (nj > 0) {
-                auto run = [&](auto &sink) {
-                    Walk wf;
-                    greedy_walk(ptu, 1, fixedpos, P.tree, wf);  // selection among the fixed lines
-                    live_sweep<MAXM>(ptu, wf.sel, nj, it, sl, lamf[k], P.tree, k, sink);
-                };
-                if (MODE == MODE_HIST) {
-                    WindowSink ws = make_window_sink(P, S, L, smem);
-                    run(ws);
-                } else {
-                    RefineSink rs = make_refine_sink(P, S, L, smem);
-                    run(rs);
-                }
+            auto run = [&](auto &sink) {
+                Walk wf;
+                greedy_walk(ptu, 1, fixedpos, P.tree, wf);  // selection among the fixed lines
+                live_sweep<MAXM>(ptu, wf.sel, nj, it, sl, lamk, P.tree, k, sink);
+            };
+            if (MODE == MODE_HIST) {
+                WindowSink ws = make_window_sink(P, S, L, smem);
+                run(ws);
+            } else {
+                RefineSink rs = make_refine_sink(P, S, L, smem);
+                run(rs);
             }
         }
+        }
+        __syncwarp();
     }
     __syncthreads();
 }
 
 template <int MAXM, int MODE, int THREADS>
-__global__ void __launch_bounds__(THREADS) dense_pass_kernel(Params P, Scratch S, const double *lam,
+__global__ void __launch_bounds__(THREADS, 2) dense_pass_kernel(Params P, Scratch S, const double *lam,
                                                              uint32_t *x_bits, int round, int T) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
@@ -1315,7 +1335,7 @@ __global__ void __launch_bounds__(THREADS) dense_pass_kernel(Params P, Scratch S
 // the next instance's parameters and multipliers.  Every sum is an integer
 // sum, so the result does not depend on which block took which tile.
 template <int MAXM, int MODE, int THREADS>
-__global__ void __launch_bounds__(THREADS) dense_batch_kernel(BatchDev B, const double *lam_all,
+__global__ void __launch_bounds__(THREADS, 2) dense_batch_kernel(BatchDev B, const double *lam_all,
                                                               uint32_t *x_all, int round) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Params sP;
