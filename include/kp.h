@@ -169,6 +169,19 @@ kp_status kp_threshold_select(kp_problem *h, const double *lambda, double *lambd
 kp_status kp_scd_step(kp_problem *h, const double *lambda, double *lambda_next, double *R,
                       double *dual_sum, double *primal_sum, void *stream);
 
+/* One block coordinate-descent iteration (Sec. 4.3.2, the variants of
+ * Algorithm 4 that update one multiplier, cyclic CD, or a block of them, block
+ * CD): for every k with block[k] != 0 (block: device uint8 [K]) the Reduce of
+ * Algorithm 4 at lambda,
+ *   lambda_next_k = min { v in {0} U {breakpoints} : sum_{v1 > v} v2 <= B_k },
+ * and lambda_next_k = lambda_k for the others.  Only the breakpoints of the
+ * block's knapsacks are computed.  With every block[k] = 1 this is
+ * kp_scd_step; with one k it is a step of cyclic CD.  dual_sum and
+ * primal_sum (nullable) as in kp_scd_breakpoints; lambda_next must not alias
+ * lambda. */
+kp_status kp_bcd_step(kp_problem *h, const double *lambda, const uint8_t *block, double *lambda_next,
+                      double *dual_sum, double *primal_sum, void *stream);
+
 /* Gradient of the dual g(lambda, p, B) of Eq. (5) by Danskin's theorem at the
  * maximiser x* (from kp_solve_users / kp_reduce_consumption at the same
  * lambda), each scaled by the device float64 scalar *upstream:

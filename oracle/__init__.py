@@ -235,6 +235,16 @@ def scd_step(p, b, S, C, lam, B):
     return out, nemit, mass
 
 
+def bcd_step(p, b, S, C, lam, B, block):
+    """One block coordinate-descent iteration (Sec. 4.3.2): the Reduce of Algorithm 4
+    at lam for the knapsacks in `block` (boolean [K]), lam unchanged elsewhere
+    (composition of scd_step)."""
+    lam = _f64(lam)
+    nxt, _, _ = scd_step(p, b, S, C, lam, B)
+    block = np.asarray(block, dtype=bool)
+    return np.where(block, nxt, lam)
+
+
 def presolve(p, b, S, C, B, users, iters):
     """Sec. 5.3 pre-solving by sampling: `iters` steps of Algorithm 4 from lambda = 0
     on the users `users` with every budget scaled by n / N (composition of the

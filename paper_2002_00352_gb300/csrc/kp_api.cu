@@ -407,6 +407,17 @@ kp_status kp_scd_step(kp_problem *h, const double *lambda, double *lambda_next, 
     return kp_threshold_select(h, lambda, lambda_next, stream);
 }
 
+kp_status kp_bcd_step(kp_problem *h, const double *lambda, const uint8_t *block, double *lambda_next,
+                      double *dual_sum, double *primal_sum, void *stream) {
+    if (!check_handle(h) || !lambda || !block || !lambda_next) return fail(KP_EINVAL, "kp_bcd_step: NULL argument");
+    if (lambda == lambda_next) return fail(KP_EINVAL, "kp_bcd_step: lambda_next must not alias lambda");
+    h->S.block = block;  // copied into every launch below
+    kp_status s = kp_scd_breakpoints(h, lambda, nullptr, dual_sum, primal_sum, nullptr, stream);
+    if (s == KP_OK) s = kp_threshold_select(h, lambda, lambda_next, stream);
+    h->S.block = nullptr;
+    return s;
+}
+
 kp_status kp_dual_backward(kp_problem *h, const double *lambda, const uint32_t *x_bits,
                            const double *R, const double *upstream, double *grad_lambda,
                            float *grad_p, double *grad_B, void *stream) {

@@ -99,6 +99,8 @@ struct Scratch {
                                       // that three or more items of one user use
     int64_t nrare;
     int32_t rare_blk0, rare_grid;     // buffer blocks [rare_blk0, +rare_grid) of the rare-knapsack kernel
+    const uint8_t *block;             // [K] device, knapsacks a block coordinate-descent step updates
+                                      // (nullptr: all of them, Algorithm 4)
 };
 
 enum PassMode { MODE_STATE = 0, MODE_HIST = 1, MODE_REFINE = 2 };

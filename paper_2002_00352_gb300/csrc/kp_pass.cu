@@ -149,7 +149,11 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
             // regular CSR rows also need the breakpoints above lambda_k^t
             const float wlf = __uint_as_float(wlo);
             const float fl = P.layout == KP_B_DENSE ? wlf : fminf(wlf, lf);
-            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, wlf, __uint_as_float(whi), low_bound(fl, lf));
+            // a knapsack outside the block of a block coordinate-descent step
+            // gets no breakpoints (its floor is +inf)
+            const bool inb = S.block == nullptr || S.block[k] != 0;
+            ((float4 *)(smem + L.kinfo))[k] =
+                make_float4(lf, wlf, __uint_as_float(whi), inb ? low_bound(fl, lf) : __int_as_float(0x7f800000));
             const SFix r6{(uint32_t *)(smem + L.reg3), 6 * K};
 #pragma unroll
             for (int q = 0; q < 6; ++q) r6.zero(q * K + k);
@@ -1248,7 +1252,7 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
                 acc += bmass(bcol[(size_t)j * K], P.bscale);
             }
             if (acc) rfix.add64(k, acc);
-            if (MODE == MODE_HIST) {
+            if (MODE == MODE_HIST && tk < __int_as_float(0x7f800000)) {
                 // the user's whole emitted mass, its k-consumption as lambda_k -> 0+
                 // (Algorithm 1 at lambda_k = 0; at lambda_k^t = 0 the consumption
                 // above): the selection reads it to decide lambda_k = 0, so the

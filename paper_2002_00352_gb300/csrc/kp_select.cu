@@ -191,6 +191,16 @@ __device__ __forceinline__ void select_body(const Params &P, Scratch &S, int k, 
     __shared__ unsigned long long row[NSUB];
     __shared__ int s_pick;
     __shared__ unsigned long long s_above;
+    if (S.block && !S.block[k]) {  // outside the block of a block coordinate-descent step
+        if (round == 0 && threadIdx.x == 0) {
+            lam_next[k] = lam[k];
+            S.reg3[3 * k] = 0ull;
+            S.reg3[3 * k + 1] = 0ull;
+            S.reg3[3 * k + 2] = 0ull;
+            S.ovf[k] = 0u;
+        }
+        return;
+    }
     if (threadIdx.x == 0) sk = S.sel[k];
     __syncthreads();
     if (round > 0 && sk.state != 1) return;

@@ -57,7 +57,7 @@ EXPORTS = [
     "kp_version",
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
-    "kp_autotune", "kp_limits",
+    "kp_autotune", "kp_limits", "kp_bcd_step",
 ]
 
 
@@ -93,6 +93,7 @@ def load_library(path: Optional[str] = None):
     lib.kp_batch_device_status.argtypes = [P, P]
     lib.kp_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int32), P]
     lib.kp_limits.argtypes = [ctypes.POINTER(ctypes.c_int32)]
+    lib.kp_bcd_step.argtypes = [P, P, P, P, P, P, P]
     lib.kp_last_error.restype = ctypes.c_char_p
     lib.kp_version.restype = ctypes.c_int
     for name in EXPORTS:
@@ -273,6 +274,14 @@ def kp_scd_step(prob: Problem, lam, lam_next, R=None, dual_sum=None, primal_sum=
         prob.handle, _ptr(lam, torch.float64, "lambda"), _ptr(lam_next, torch.float64, "lambda_next"),
         _ptr(R, torch.float64, "R"), _ptr(dual_sum, torch.float64, "dual_sum"),
         _ptr(primal_sum, torch.float64, "primal_sum"), _stream(stream)))
+
+
+def kp_bcd_step(prob: Problem, lam, block, lam_next, dual_sum=None, primal_sum=None, stream=None):
+    """Block / cyclic coordinate descent (Sec. 4.3.2): block = uint8 [K] device flags."""
+    _check(load_library().kp_bcd_step(prob.handle, _ptr(lam, torch.float64, "lambda"), _ptr(block, torch.uint8, "block"),
+                                      _ptr(lam_next, torch.float64, "lambda_next"),
+                                      _ptr(dual_sum, torch.float64, "dual_sum"),
+                                      _ptr(primal_sum, torch.float64, "primal_sum"), _stream(stream)))
 
 
 def kp_dual_backward(prob: Problem, lam, x_bits, R, upstream, grad_lambda=None, grad_p=None,

@@ -57,6 +57,29 @@ def dd_solve(prob, lam0: torch.Tensor, alpha: float, iters: int, record: bool = 
     return a, hist
 
 
+def cd_solve(prob, lam0: torch.Tensor, blocks, record: bool = False):
+    """Block coordinate descent (Sec. 4.3.2): one kp_bcd_step per entry of
+    `blocks`, each a collection of knapsack indices updated together (cyclic CD:
+    blocks = [[0], [1], ..., [K-1]] repeated; SCD: every block = all of them)."""
+    a = lam0.clone()
+    b = torch.empty_like(a)
+    mask = torch.zeros(prob.K, dtype=torch.uint8, device=a.device)
+    hist = [a.cpu()] if record else None
+    for blk in blocks:
+        mask.zero_()
+        mask[torch.as_tensor(list(blk), dtype=torch.int64, device=a.device)] = 1
+        kp.kp_bcd_step(prob, a, mask, b)
+        a, b = b, a
+        if record:
+            hist.append(a.cpu())
+    return a, hist
+
+
+def cyclic_blocks(K: int, sweeps: int):
+    """The blocks of cyclic CD: one multiplier at a time, k = 0..K-1, `sweeps` times."""
+    return [[k] for _ in range(sweeps) for k in range(K)]
+
+
 def presolve(prob, n: int, iters: int, seed: int = 0) -> torch.Tensor:
     """Sec. 5.3: lambda^0 from `iters` SCD iterations on about n users drawn
     uniformly (seeded; n draws, repeats dropped), budgets scaled by the sample's
