@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-post", action="store_true", help="skip the post-processing measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched measurement")
+    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--batch-warmup", type=int, default=1)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-nhi", type=int, default=1_000_000)
     return ap.parse_args()
@@ -270,14 +273,15 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
-def run_batched(args):
-    """256 independent dense instances (N log-uniform in [1e3, 1e6], M in 5..50, K in 1..64,
-    total cap C in 1..M/2): SCD steps of the whole batch by the batched path, and the
-    same steps by looping the per-instance path over the instances."""
+def batched_measure(count, n_hi, steps, warmup, graph=True):
+    """`count` independent dense instances (N log-uniform in [1e3, n_hi], M in 5..50,
+    K in 1..64, total cap C in 1..M/2): SCD steps of the whole batch by the batched
+    path (one persistent launch per pass), and the same steps by looping the
+    per-instance path over the instances, from lambda = 0 (warm-up steps first);
+    instances*iters/s of both and whether their lambdas agree bit for bit."""
     import torch
     from paper_2002_00352_gb300 import gen, kp
-    torch.cuda.set_device(0)
-    specs = gen.batched_specs(count=args.batch_count, n_hi=args.batch_nhi)
+    specs = gen.batched_specs(count=count, n_hi=n_hi)
     insts = [gen.batched_instance(sp, device="cuda") for sp in specs]
     batch = kp.kp_batch_create(insts)
     probs = [kp.kp_create_from_instance(x) for x in insts]
@@ -314,15 +318,15 @@ def run_batched(args):
     graph_cache = {}
     res = {}
     modes = [("batched", batched_steps), ("looped", looped_steps)]
-    if args.steps % 2 == 0 and args.warmup % 2 == 0:
+    if graph and steps % 2 == 0 and warmup % 2 == 0:
         modes.append(("graph", graph_steps))
     for name, fn in modes:
         lam = torch.zeros(totK, dtype=torch.float64, device="cuda")
-        lam = fn(args.warmup, lam)
+        lam = fn(warmup, lam)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        lam = fn(args.steps, lam)
+        lam = fn(steps, lam)
         e1.record()
         torch.cuda.synchronize()
         res[name] = (e0.elapsed_time(e1), lam.cpu())
@@ -330,21 +334,33 @@ def run_batched(args):
     same = bool(torch.equal(res["batched"][1], res["looped"][1]))
     ms_b, ms_l = res["batched"][0], res["looped"][0]
     n = len(insts)
-    users = sum(x.N for x in insts)
-    out = {"metric": "batched SCD instances*iters/s (256 instances)", "value": n * args.steps / (ms_b / 1e3),
-           "unit": "instances*iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": ms_b / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"{n} dense instances, N log-uniform [1e3, {args.batch_nhi:.0e}], M 5..50, "
-                                  f"K 1..64, total cap 1..M/2", "users": users, "total_knapsacks": totK,
-                      "instance_bytes": sum(x.nbytes() for x in insts),
-                      "looped_value": n * args.steps / (ms_l / 1e3), "looped_ms_per_step": ms_l / args.steps,
-                      "speedup_vs_looped": ms_l / ms_b, "same_lambda_as_looped": same}}
+    out = {"metric": f"batched SCD instances*iters/s ({n} instances)", "value": n * steps / (ms_b / 1e3),
+           "unit": "instances*iters/s", "steps": steps, "warmup": warmup, "ms_per_step": ms_b / steps,
+           "workload": f"{n} dense instances, N log-uniform [1e3, {n_hi:.0e}], M 5..50, K 1..64, "
+                       f"total cap 1..M/2, SCD from lambda = 0 ({warmup} warm-up steps)",
+           "users": sum(x.N for x in insts), "total_knapsacks": totK,
+           "instance_bytes": sum(x.nbytes() for x in insts),
+           "looped_value": n * steps / (ms_l / 1e3), "looped_ms_per_step": ms_l / steps,
+           "speedup_vs_looped": ms_l / ms_b, "same_lambda_as_looped": same}
     if "graph" in res:
         ms_g = res["graph"][0]
-        out["config"]["graph_ms_per_step"] = ms_g / args.steps
-        out["config"]["graph_value"] = n * args.steps / (ms_g / 1e3)
-        out["config"]["same_lambda_graph"] = bool(torch.equal(res["graph"][1], res["batched"][1]))
+        out["graph_ms_per_step"] = ms_g / steps
+        out["graph_value"] = n * steps / (ms_g / 1e3)
+        out["same_lambda_graph"] = bool(torch.equal(res["graph"][1], res["batched"][1]))
+    del batch, probs, insts, graph_cache
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    b = batched_measure(args.batch_count, args.batch_nhi, args.steps, args.warmup)
+    out = {"metric": b["metric"], "value": b["value"], "unit": b["unit"], "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {k: v for k, v in b.items() if k not in ("metric", "value", "unit", "steps", "warmup",
+                                                              "ms_per_step")}}
     print(json.dumps(out), flush=True)
 
 
@@ -561,6 +577,20 @@ def main():
             result["cpu_baseline"] = cpu_baseline(inst, min(args.cpu_sample, N))
         except Exception as e:  # pragma: no cover
             result["cpu_baseline"] = {"value": None, "error": str(e)}
+    # batched instances (the workload of many uneven instances), after the
+    # headline instance is freed
+    if not args.no_batch and rank == 0 and args.workload.startswith("csr"):
+        try:
+            prob.close()
+        except Exception:
+            pass
+        del inst, gp, xb
+        torch.cuda.empty_cache()
+        try:
+            result["batched"] = batched_measure(args.batch_count, args.batch_nhi, args.batch_steps,
+                                                args.batch_warmup, graph=False)
+        except Exception as e:  # pragma: no cover
+            result["batched"] = {"error": str(e)}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -96,3 +96,50 @@ def test_batch_graph_replay_equals_eager():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(g.lam, a)
+
+
+def test_batch_config_shape():
+    """The batched workload's own shapes (N log-uniform up to 1e6, M 5..50, K 1..64,
+    one total cap C in 1..M/2), on 24 of its instances: three SCD steps from lambda = 0
+    by the batched path equal the per-instance path bit for bit; at the last
+    lambda^t, sampled users' decisions of every instance against the oracle's
+    greedy, and the whole step of the three smallest instances against the oracle's
+    Algorithm 4 (1e-5 relative plus the local FP32 floor)."""
+    from tests.gpu_util import check_scd_step, excused_users, floor_ulps
+    specs = gen.batched_specs(count=256, n_hi=1_000_000)[:24]
+    insts = [gen.batched_instance(sp, device="cuda") for sp in specs]
+    batch = kp.kp_batch_create(insts)
+    probs = [kp.kp_create_from_instance(x) for x in insts]
+    lam = torch.zeros(batch.totK, dtype=torch.float64, device="cuda")
+    for step in range(3):
+        nxt = torch.zeros_like(lam)
+        kp.kp_batch_scd_step(batch, lam, nxt)
+        kp.kp_batch_device_status(batch)
+        loop = torch.zeros_like(lam)
+        for i, pr in enumerate(probs):
+            a, b = batch.koff[i], batch.koff[i + 1]
+            kp.kp_scd_step(pr, lam[a:b].contiguous(), loop[a:b])
+            kp.kp_device_status(pr)
+        assert torch.equal(loop, nxt), step
+        if step < 2:
+            lam = nxt
+    lam_h = lam.cpu().numpy()
+    got = nxt.cpu().numpy()
+    rng = np.random.default_rng(9)
+    for i, (x, pr) in enumerate(zip(insts, probs)):
+        a, b = batch.koff[i], batch.koff[i + 1]
+        idx = np.sort(rng.choice(x.N, size=min(300, x.N), replace=False))
+        p, bb = x.users_dense(idx)
+        xb = kp.kp_solve_users(pr, lam[a:b].contiguous())
+        xs = kp.unpack_x(xb.view(x.N, -1)[torch.as_tensor(idx, device="cuda")].reshape(-1), len(idx), x.M).cpu().numpy()
+        xo, _, _, _ = oracle.user_pass(p, bb, x.S, x.C, lam_h[a:b])
+        exc = excused_users(p, bb, lam_h[a:b])
+        assert np.array_equal(xs[~exc], xo[~exc]), i
+    for i in np.argsort([x.N * x.M * x.K for x in insts])[:3]:
+        x = insts[i]
+        a, b = batch.koff[i], batch.koff[i + 1]
+        p, bb = x.to_dense_numpy()
+        want, _, _ = oracle.scd_step(p, bb, x.S, x.C, lam_h[a:b], x.B.cpu().numpy())
+        emis = oracle.scd_map_users(p, bb, x.S, x.C, lam_h[a:b])
+        check_scd_step(got[a:b], want, p, bb, lam_h[a:b], emis, floor_ulps("dense", x.K), label=f"batch inst {i}",
+                       max_loose_share=1.0)
