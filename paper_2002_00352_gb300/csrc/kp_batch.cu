@@ -180,8 +180,10 @@ kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out) {
     std::vector<kp::Scratch> hS(count);
     for (int i = 0; i < count && st == KP_OK; ++i) {
         kp_problem *h = b->probs[i];
+        // the breakpoint buffer of a single handle (kp_create): a smaller one
+        // overflows on large instances and costs re-run passes
         double budget = 4.0 * (double)h->P.N * h->P.M;
-        budget = std::min(std::max(budget, (double)(1 << 16)), (double)(1 << 24));
+        budget = std::min(std::max(budget, (double)(1 << 20)), (double)(1 << 28));
         st = kp_impl::alloc_scratch(h, b->G, 0, b->G, budget, b->ctr + i,
                                     b->bufcnt + (size_t)b->koff[i] * b->G);
         hP[i] = h->P;
