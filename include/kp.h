@@ -226,6 +226,30 @@ kp_status kp_batch_scd_step(kp_batch *b, const double *lambda, double *lambda_ne
 /* As kp_device_status, over every instance of the batch. */
 kp_status kp_batch_device_status(kp_batch *b, void *stream);
 
+/* ------------------------------------------------------------------------
+ * User-sharded instances: one instance whose users are split over several
+ * handles (shards; on several GPUs, one per device), solved as one.  Users are
+ * independent given lambda (Sec. 4.1, the Map of Algorithms 2 and 4), so each
+ * shard runs the user passes of its own users and the Reduce combines the
+ * shards' exact integer partials (fixed-point consumption and objective sums,
+ * window masses, sub-histograms) and their buffered breakpoints: the result is
+ * that of one handle over all the users, bit for bit.
+ *   - Each shard is created with kp_create over its range of users (p, b and
+ *     the CSR rows of those users; the same K, M, local sets and budgets B).
+ *   - kp_shard_group_create sets one fixed-point unit for all shards (the one
+ *     a single handle would choose for the union) and keeps the handles; they
+ *     must outlive the group and be used through it only.  All shards must be
+ *     on the current device (the lead's kernels read the others' scratch).
+ *   - kp_shard_group_scd_step is kp_scd_step over the union; the selection
+ *     state lives in shard 0 (the lead) and is copied to the others.
+ * ------------------------------------------------------------------------ */
+typedef struct kp_shard_group kp_shard_group;
+
+kp_status kp_shard_group_create(kp_problem *const *shards, int32_t n, kp_shard_group **out);
+kp_status kp_shard_group_destroy(kp_shard_group *g);
+kp_status kp_shard_group_scd_step(kp_shard_group *g, const double *lambda, double *lambda_next, double *R,
+                                  double *dual_sum, double *primal_sum, void *stream);
+
 /* Allocation-free form of kp_reduce_consumption, for callers that cannot
  * allocate device memory: a process whose device memory belongs to its own
  * pool (an outside cudaMalloc would fail or fragment it), or code on a

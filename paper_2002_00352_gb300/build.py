@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkp.so")
-SOURCES = ["kp_api.cu", "kp_pass.cu", "kp_select.cu", "kp_noalloc.cu", "kp_batch.cu", "kp_presolve.cu", "kp_postprocess.cu"]
+SOURCES = ["kp_api.cu", "kp_pass.cu", "kp_select.cu", "kp_noalloc.cu", "kp_batch.cu", "kp_presolve.cu", "kp_postprocess.cu",
+           "kp_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]

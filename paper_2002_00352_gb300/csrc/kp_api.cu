@@ -188,11 +188,14 @@ kp_status fill_params(const kp_desc *d, kp::Params &P, uint32_t *flags, cudaStre
         }
     }
     // fixed-point mass: every per-knapsack sum is below count * max b
+    P.entries = count;
+    P.maxb = maxb;
     P.fixs = kp::mass_shift(count, maxb);
     P.bscale = std::ldexp(1.0f, P.fixs);
     // objective sums: every per-user value is below M * max p
     float maxp;
     memcpy(&maxp, &hf[2], 4);
+    P.maxp = maxp;
     double bo = (double)P.N * P.M * (double)maxp + 1.0;
     int so = (int)std::floor(62.0 - std::log2(bo));
     if (so > 40) so = 40;

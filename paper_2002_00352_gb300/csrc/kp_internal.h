@@ -75,6 +75,8 @@ struct Params {
     int32_t creg;              // CSR: every item has exactly creg entries (0: not regular)
     int32_t vec;               // CSR regular rows aligned for vector loads (M in {8, 10, 16})
     int64_t uoff0;             // csr_user_off[0]
+    double entries;            // b entries summed per knapsack (the count the unit 2^-fixs allows for)
+    float maxb, maxp;          // largest b and p of the instance
     Tree tree;
 };
 
@@ -101,6 +103,8 @@ struct Scratch {
     int32_t rare_blk0, rare_grid;     // buffer blocks [rare_blk0, +rare_grid) of the rare-knapsack kernel
     const uint8_t *block;             // [K] device, knapsacks a block coordinate-descent step updates
                                       // (nullptr: all of them, Algorithm 4)
+    const struct Scratch *peers;      // [npeers] device: the other shards of a user-sharded instance,
+    int32_t npeers;                   // whose integer partials and buffers the lead's selection also reads
 };
 
 enum PassMode { MODE_STATE = 0, MODE_HIST = 1, MODE_REFINE = 2 };

@@ -42,7 +42,14 @@ __device__ __forceinline__ void finalize_body(const Params &P, const Scratch &S,
     const int K = P.K;
     if (threadIdx.x == 0) {
         const double io = ldexp(1.0, -P.fixo);
-        const double a = (double)S.objfix[0] * io, b = (double)S.objfix[1] * io;
+        unsigned long long o0 = S.objfix[0], o1 = S.objfix[1];
+        for (int q = 0; q < S.npeers; ++q) {  // the other shards' users
+            o0 += S.peers[q].objfix[0];
+            o1 += S.peers[q].objfix[1];
+            S.peers[q].objfix[0] = 0ull;
+            S.peers[q].objfix[1] = 0ull;
+        }
+        const double a = (double)o0 * io, b = (double)o1 * io;
         S.objfix[0] = 0ull;
         S.objfix[1] = 0ull;
         if (dual) *dual = a;
@@ -56,7 +63,12 @@ __device__ __forceinline__ void finalize_body(const Params &P, const Scratch &S,
     __syncthreads();
     const double inv = ldexp(1.0, -P.fixs);
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const double Rk = (double)S.Rfix[k] * inv;
+        unsigned long long rf = S.Rfix[k];
+        for (int q = 0; q < S.npeers; ++q) {
+            rf += S.peers[q].Rfix[k];
+            S.peers[q].Rfix[k] = 0ull;
+        }
+        const double Rk = (double)rf * inv;
         S.Rfix[k] = 0ull;
         if (R) R[k] = Rk;
         if (do_dd) {
@@ -112,13 +124,17 @@ __device__ uint32_t exact_select(const Scratch &S, const Params &P, int k, uint3
         const int nd = (int)(((width - 1) >> sh) + 1);
         for (int d = threadIdx.x; d < NSUB; d += blockDim.x) h[d] = 0ull;
         __syncthreads();
-        for (int gblk = 0; gblk < S.gspan; ++gblk) {
-            const uint32_t cnt = S.bufcnt[(size_t)k * S.gspan + gblk];
-            const uint2 *base = S.buf + ((size_t)k * S.gspan + gblk) * S.cap_kb;
-            for (uint32_t s = threadIdx.x; s < cnt; s += blockDim.x) {
-                const uint2 e = base[s];
-                const uint32_t off = e.x - clo;
-                if (e.x >= clo && off < width) atomicAdd(&h[off >> sh], (unsigned long long)bmass(__uint_as_float(e.y), P.bscale));
+        for (int q = -1; q < S.npeers; ++q) {  // this shard's buffer, then the other shards'
+            const Scratch &T = q < 0 ? S : S.peers[q];
+            for (int gblk = 0; gblk < T.gspan; ++gblk) {
+                const uint32_t cnt = T.bufcnt[(size_t)k * T.gspan + gblk];
+                const uint2 *base = T.buf + ((size_t)k * T.gspan + gblk) * T.cap_kb;
+                for (uint32_t s = threadIdx.x; s < cnt; s += blockDim.x) {
+                    const uint2 e = base[s];
+                    const uint32_t off = e.x - clo;
+                    if (e.x >= clo && off < width)
+                        atomicAdd(&h[off >> sh], (unsigned long long)bmass(__uint_as_float(e.y), P.bscale));
+                }
             }
         }
         __syncthreads();
@@ -206,20 +222,32 @@ __device__ __forceinline__ void select_body(const Params &P, Scratch &S, int k, 
     if (round > 0 && sk.state != 1) return;
     const unsigned long long Bfix = budget_fixed(P.B[k], P.fixs);
     const float lam_t = (float)lam[k];
-    const uint32_t ovf = S.ovf[k];
+    uint32_t ovf = S.ovf[k];
+    for (int q = 0; q < S.npeers; ++q) ovf |= S.peers[q].ovf[k];
     __syncthreads();
     if (threadIdx.x == 0) {
         S.ovf[k] = 0u;
+        for (int q = 0; q < S.npeers; ++q) S.peers[q].ovf[k] = 0u;
         if (ovf) atomicAdd(&S.ctr->stats[2], 1ull);
     }
     if (round == 0) {
-        // masses at/above, inside and below the window [wlo, whi)
-        const unsigned long long A = S.reg3[3 * k], W = S.reg3[3 * k + 1], Bl = S.reg3[3 * k + 2];
+        // masses at/above, inside and below the window [wlo, whi), summed over the shards
+        unsigned long long A = S.reg3[3 * k], W = S.reg3[3 * k + 1], Bl = S.reg3[3 * k + 2];
+        for (int q = 0; q < S.npeers; ++q) {
+            A += S.peers[q].reg3[3 * k];
+            W += S.peers[q].reg3[3 * k + 1];
+            Bl += S.peers[q].reg3[3 * k + 2];
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             S.reg3[3 * k] = 0ull;
             S.reg3[3 * k + 1] = 0ull;
             S.reg3[3 * k + 2] = 0ull;
+            for (int q = 0; q < S.npeers; ++q) {
+                S.peers[q].reg3[3 * k] = 0ull;
+                S.peers[q].reg3[3 * k + 1] = 0ull;
+                S.peers[q].reg3[3 * k + 2] = 0ull;
+            }
         }
         // dense rows: Bl is the total mass (every user's consumption as
         // lambda_k -> 0+).  Regular CSR rows leave out of Bl the breakpoints
@@ -269,8 +297,14 @@ __device__ __forceinline__ void select_body(const Params &P, Scratch &S, int k, 
     // refine round: sub-histogram of [sk.lo, sk.hi)
     unsigned long long *grow = S.subhist + (size_t)k * NSUB;
     for (int q = threadIdx.x; q < NSUB; q += blockDim.x) {
-        row[q] = grow[q];
+        unsigned long long v = grow[q];
         grow[q] = 0ull;
+        for (int r = 0; r < S.npeers; ++r) {  // the other shards' sub-histograms
+            unsigned long long *pg = S.peers[r].subhist + (size_t)k * NSUB;
+            v += pg[q];
+            pg[q] = 0ull;
+        }
+        row[q] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

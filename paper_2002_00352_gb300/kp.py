@@ -57,7 +57,8 @@ EXPORTS = [
     "kp_version",
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
-    "kp_autotune", "kp_limits", "kp_bcd_step",
+    "kp_autotune", "kp_limits", "kp_bcd_step", "kp_shard_group_create", "kp_shard_group_destroy",
+    "kp_shard_group_scd_step",
 ]
 
 
@@ -94,6 +95,9 @@ def load_library(path: Optional[str] = None):
     lib.kp_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int32), P]
     lib.kp_limits.argtypes = [ctypes.POINTER(ctypes.c_int32)]
     lib.kp_bcd_step.argtypes = [P, P, P, P, P, P, P]
+    lib.kp_shard_group_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32, ctypes.POINTER(ctypes.c_void_p)]
+    lib.kp_shard_group_destroy.argtypes = [P]
+    lib.kp_shard_group_scd_step.argtypes = [P, P, P, P, P, P, P]
     lib.kp_last_error.restype = ctypes.c_char_p
     lib.kp_version.restype = ctypes.c_int
     for name in EXPORTS:
@@ -422,3 +426,49 @@ def kp_batch_scd_step(batch: Batch, lam, lam_next, stream=None):
 
 def kp_batch_device_status(batch: Batch, stream=None):
     _check(load_library().kp_batch_device_status(batch.handle, _stream(stream)))
+
+
+class ShardGroup:
+    """A kp_shard_group: one instance whose users are split over several handles."""
+
+    def __init__(self, handle, shards):
+        self.handle = handle
+        self.shards = shards    # keeps the handles (and their instances) alive
+        self.K = shards[0].K
+
+    def close(self):
+        if self.handle:
+            load_library().kp_shard_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kp_shard_group_create(shards) -> ShardGroup:
+    arr = (ctypes.c_void_p * len(shards))(*[s.handle for s in shards])
+    out = ctypes.c_void_p()
+    _check(load_library().kp_shard_group_create(arr, len(shards), ctypes.byref(out)))
+    return ShardGroup(out, list(shards))
+
+
+def kp_shard_group_scd_step(group: ShardGroup, lam, lam_next, R=None, dual_sum=None, primal_sum=None,
+                            stream=None):
+    _check(load_library().kp_shard_group_scd_step(group.handle, _ptr(lam, torch.float64, "lambda"),
+                                                  _ptr(lam_next, torch.float64, "lambda_next"),
+                                                  _ptr(R, torch.float64, "R"),
+                                                  _ptr(dual_sum, torch.float64, "dual_sum"),
+                                                  _ptr(primal_sum, torch.float64, "primal_sum"), _stream(stream)))
+
+
+def kp_create_user_range(inst, u0: int, u1: int) -> Problem:
+    """A handle over the users [u0, u1) of an instance (a shard): views of their rows."""
+    M, K = inst.M, inst.K
+    p = inst.p[u0 * M:u1 * M]
+    if inst.layout == "dense":
+        return kp_create(u1 - u0, M, K, p, inst.B, inst.S, inst.C, b_dense=inst.b[u0 * M * K:u1 * M * K])
+    return kp_create(u1 - u0, M, K, p, inst.B, inst.S, inst.C, csr_user_off=inst.user_off[u0:u1 + 1],
+                     csr_item_nnz=inst.item_nnz[u0 * M:u1 * M], csr_val=inst.val, csr_k=inst.kidx)

@@ -180,7 +180,7 @@ def test_dual_gradient_fd_N2e7():
         tot = 0.0
         step = 1 << 21
         for s in range(0, N, step):
-            sl = pv[s:s + step].double() + torch.einsum("nmk,k->nm", bv[s:s + step].double(), lt)
+            sl = pv[s:s + step].detach().double() + torch.einsum("nmk,k->nm", bv[s:s + step].double(), lt)
             xs = kp.unpack_x(x.view(N, -1)[s:s + step].reshape(-1), sl.shape[0], M).double()
             e = (K / 4 + 6) * u * (sl * xs).sum(1)
             tot += float((e * e).sum())
