@@ -319,9 +319,11 @@ kp_status kp_presolve(kp_problem *h, const int64_t *users, int64_t n, int32_t it
  *   R_after  device float64 [K]: consumption of the returned x, summed in
  *            the fixed point of kp_reduce_consumption (nullable)
  * Budgets are compared in that fixed point (units of 2^-s with every entry's
- * b at most 2^30 units).  Asynchronous on the stream; takes 24 N + O(K) bytes
- * of stream-ordered device memory for the call (keys and two lists of users).  An inconsistent selection (not
- * expected) is reported as KP_ESTATE by kp_device_status. */
+ * b at most 2^30 units).  Asynchronous on the stream, except the first call
+ * on a handle, which allocates 24 N + O(K) bytes of device memory (keys and
+ * two lists of users) that the handle keeps until kp_destroy.  An
+ * inconsistent selection (not expected) is reported as KP_ESTATE by
+ * kp_device_status. */
 kp_status kp_postprocess(kp_problem *h, const double *lambda, uint32_t *x_bits, int64_t *reset,
                          double *R_after, void *stream);
 

@@ -331,6 +331,7 @@ kp_status kp_create(const kp_desc *d, kp_problem **out) {
 kp_status kp_destroy(kp_problem *h) {
     if (!h) return KP_OK;
     cudaDeviceSynchronize();
+    if (h->ppbuf) cudaFree(h->ppbuf);
     free_all(h);
     delete h;
     return KP_OK;

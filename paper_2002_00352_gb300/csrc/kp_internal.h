@@ -187,6 +187,8 @@ struct kp_problem {
     kp::Scratch S;
     int device;
     std::vector<void *> allocs;
+    unsigned long long *ppbuf = nullptr;  // post-processing scratch, allocated at its first call
+    size_t ppwords = 0;
 };
 
 namespace kp_impl {

@@ -97,55 +97,67 @@ __device__ __forceinline__ uint64_t user_x(const Params &P, const uint32_t *x, i
 }
 
 // q_i: items in ascending j, the knapsacks of an item in ascending k
+// First entry of item j of user i (CSR): with the same number creg of entries
+// per item it is computed, otherwise the counts of the items before j are summed.
+__device__ __forceinline__ int64_t item_entry(const Params &P, int64_t i, int j, int64_t &e_walk, int &j_walk) {
+    if (P.creg > 0) return P.uoff0 + (i * P.M + j) * (int64_t)P.creg;
+    while (j_walk < j) e_walk += P.innz[i * P.M + j_walk++];
+    return e_walk;
+}
+
 template <int LAYOUT>
 __device__ double group_profit(const Params &P, const double *lambda, uint64_t xm, int64_t i) {
     double q = 0.0;
-    int64_t e = LAYOUT == KP_B_CSR ? P.uoff[i] : 0;
-    for (int j = 0; j < P.M; ++j) {
-        const int n = LAYOUT == KP_B_CSR ? (int)P.innz[i * P.M + j] : 0;
-        if ((xm >> j) & 1ull) {
-            q = __dadd_rn(q, (double)P.p[i * P.M + j]);
-            if (LAYOUT == KP_B_CSR) {
-                for (int c = 0; c < n; ++c)
-                    q = __dsub_rn(q, __dmul_rn(lambda[P.kidx[e + c]], (double)P.val[e + c]));
-            } else {
-                const float *bj = P.b + (i * P.M + j) * (int64_t)P.K;
-                for (int k = 0; k < P.K; ++k) q = __dsub_rn(q, __dmul_rn(lambda[k], (double)bj[k]));
-            }
+    int64_t ew = LAYOUT == KP_B_CSR && P.creg == 0 ? P.uoff[i] : 0;
+    int jw = 0;
+    uint64_t r = xm;
+    while (r) {  // the selected items, ascending j
+        const int j = __ffsll((long long)r) - 1;
+        r &= r - 1;
+        q = __dadd_rn(q, (double)P.p[i * P.M + j]);
+        if (LAYOUT == KP_B_CSR) {
+            const int64_t e = item_entry(P, i, j, ew, jw);
+            const int n = P.creg > 0 ? P.creg : (int)P.innz[i * P.M + j];
+            for (int c = 0; c < n; ++c)
+                q = __dsub_rn(q, __dmul_rn(lambda[P.kidx[e + c]], (double)P.val[e + c]));
+        } else {
+            const float *bj = P.b + (i * P.M + j) * (int64_t)P.K;
+            for (int k = 0; k < P.K; ++k) q = __dsub_rn(q, __dmul_rn(lambda[k], (double)bj[k]));
         }
-        e += n;
     }
     return q;
 }
 
-// adds the user's consumption of knapsack k to bin[slot[k]] (every k when
-// slot is NULL; knapsacks with slot -1 are skipped)
+// adds the user's consumption of knapsack k to counter base + slot[k] of the
+// shared sums (every k when slot is NULL; knapsacks with slot -1 are skipped)
 template <int LAYOUT>
-__device__ void add_consumption(const Params &P, uint64_t xm, int64_t i, unsigned long long *bin,
+__device__ void add_consumption(const Params &P, uint64_t xm, int64_t i, const kp::SFix &bin, int base,
                                 const int32_t *slot) {
-    int64_t e = LAYOUT == KP_B_CSR ? P.uoff[i] : 0;
-    for (int j = 0; j < P.M; ++j) {
-        const int n = LAYOUT == KP_B_CSR ? (int)P.innz[i * P.M + j] : 0;
-        if ((xm >> j) & 1ull) {
-            if (LAYOUT == KP_B_CSR) {
-                for (int c = 0; c < n; ++c) {
-                    const int k = P.kidx[e + c];
-                    const int s = slot ? slot[k] : k;
-                    if (s < 0) continue;
-                    const unsigned long long m = kp::bmass(P.val[e + c], P.bscale);
-                    if (m) atomicAdd(&bin[s], m);
-                }
-            } else {
-                const float *bj = P.b + (i * P.M + j) * (int64_t)P.K;
-                for (int k = 0; k < P.K; ++k) {
-                    const int s = slot ? slot[k] : k;
-                    if (s < 0) continue;
-                    const unsigned long long m = kp::bmass(bj[k], P.bscale);
-                    if (m) atomicAdd(&bin[s], m);
-                }
+    int64_t ew = LAYOUT == KP_B_CSR && P.creg == 0 ? P.uoff[i] : 0;
+    int jw = 0;
+    uint64_t r = xm;
+    while (r) {
+        const int j = __ffsll((long long)r) - 1;
+        r &= r - 1;
+        if (LAYOUT == KP_B_CSR) {
+            const int64_t e = item_entry(P, i, j, ew, jw);
+            const int n = P.creg > 0 ? P.creg : (int)P.innz[i * P.M + j];
+            for (int c = 0; c < n; ++c) {
+                const int k = P.kidx[e + c];
+                const int s = slot ? slot[k] : k;
+                if (s < 0) continue;
+                const uint32_t m = kp::bmass(P.val[e + c], P.bscale);
+                if (m) bin.add(base + s, m);
+            }
+        } else {
+            const float *bj = P.b + (i * P.M + j) * (int64_t)P.K;
+            for (int k = 0; k < P.K; ++k) {
+                const int s = slot ? slot[k] : k;
+                if (s < 0) continue;
+                const uint32_t m = kp::bmass(bj[k], P.bscale);
+                if (m) bin.add(base + s, m);
             }
         }
-        e += n;
     }
 }
 
@@ -170,8 +182,9 @@ __device__ __forceinline__ unsigned long long warp_max(unsigned long long v) {
 template <int LAYOUT>
 __global__ void __launch_bounds__(PP_THREADS) pp_keys_kernel(const Params P, const double *lambda,
                                                              const uint32_t *x, PPWork w) {
-    extern __shared__ unsigned long long sR[];  // [K]
-    for (int k = threadIdx.x; k < P.K; k += blockDim.x) sR[k] = 0ull;
+    extern __shared__ unsigned long long smem_pp[];
+    const kp::SFix sR{(uint32_t *)smem_pp, P.K};  // [K] consumption (word pairs)
+    for (int k = threadIdx.x; k < P.K; k += blockDim.x) sR.zero(k);
     __syncthreads();
     unsigned long long lo = ~0ull, hi = 0ull;
     const int lane = threadIdx.x & 31;
@@ -180,11 +193,11 @@ __global__ void __launch_bounds__(PP_THREADS) pp_keys_kernel(const Params P, con
         const int64_t i = b0 + lane;
         if (i < P.N) {
             const uint64_t xm = user_x(P, x, i);
-            const unsigned long long key = ordered_key(group_profit<LAYOUT>(P, lambda, xm, i));
+            const unsigned long long key = ordered_key(xm ? group_profit<LAYOUT>(P, lambda, xm, i) : 0.0);
             w.ukey[i] = key;
             lo = key < lo ? key : lo;
             hi = key > hi ? key : hi;
-            if (xm) add_consumption<LAYOUT>(P, xm, i, sR, nullptr);
+            if (xm) add_consumption<LAYOUT>(P, xm, i, sR, 0, nullptr);
         }
     }
     lo = warp_min(lo);
@@ -195,7 +208,7 @@ __global__ void __launch_bounds__(PP_THREADS) pp_keys_kernel(const Params P, con
     }
     __syncthreads();
     for (int k = threadIdx.x; k < P.K; k += blockDim.x) {
-        const unsigned long long v = sR[k];
+        const unsigned long long v = sR.get(k);
         if (v) atomicAdd(&w.Rfix[k], v);
     }
 }
@@ -253,12 +266,13 @@ __global__ void __launch_bounds__(PPF_THREADS) pp_start_kernel(PPWork w, const d
 template <int LAYOUT>
 __global__ void __launch_bounds__(PP_THREADS) pp_level_kernel(const Params P, const uint32_t *x, PPWork w,
                                                               int level, int ib) {
-    extern __shared__ unsigned long long sbin[];  // [nd][nact] sums, [nd] counts, then slots
+    extern __shared__ unsigned long long smem_pp[];  // [nd][nact] sums, [nd] counts (word pairs), then slots
     const PPState s = *w.st;
     if (s.phase != 0) return;
     const int nact = s.nact, nd = 1 << s.dbits, nb = nd * nact + nd;
-    int32_t *slot = (int32_t *)(sbin + nb);
-    for (int q = threadIdx.x; q < nb; q += blockDim.x) sbin[q] = 0ull;
+    const kp::SFix sbin{(uint32_t *)smem_pp, nb};
+    int32_t *slot = (int32_t *)(smem_pp + nb);
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) sbin.zero(q);
     for (int k = threadIdx.x; k < P.K; k += blockDim.x) slot[k] = w.kslot[k];
     __syncthreads();
     const int cut = s.cut, pos = cut > s.dbits ? cut - s.dbits : 0;
@@ -292,13 +306,13 @@ __global__ void __launch_bounds__(PP_THREADS) pp_level_kernel(const Params P, co
         }
         if (!match) continue;
         const int d = (int)((unsigned)(uint64_t)(c >> pos) & dmask);
-        atomicAdd(&sbin[nd * nact + d], 1ull);
+        sbin.add(nd * nact + d, 1u);
         const uint64_t xm = user_x(P, x, i);
-        if (xm) add_consumption<LAYOUT>(P, xm, i, sbin + (size_t)d * nact, slot);
+        if (xm) add_consumption<LAYOUT>(P, xm, i, sbin, d * nact, slot);
     }
     __syncthreads();
     for (int q = threadIdx.x; q < nb; q += blockDim.x) {
-        const unsigned long long v = sbin[q];
+        const unsigned long long v = sbin.get(q);
         if (v) atomicAdd(&w.bins[q], v);
     }
 }
@@ -368,9 +382,10 @@ __global__ void __launch_bounds__(PPF_THREADS) pp_select_kernel(PPWork w, int le
 // consumption they release
 template <int LAYOUT>
 __global__ void __launch_bounds__(PP_THREADS) pp_clear_kernel(const Params P, uint32_t *x, PPWork w, int ib) {
-    extern __shared__ unsigned long long sR[];  // [K]
+    extern __shared__ unsigned long long smem_pp[];
+    const kp::SFix sR{(uint32_t *)smem_pp, P.K};  // [K] released consumption (word pairs)
     if (w.st->phase != 2) return;
-    for (int k = threadIdx.x; k < P.K; k += blockDim.x) sR[k] = 0ull;
+    for (int k = threadIdx.x; k < P.K; k += blockDim.x) sR.zero(k);
     __syncthreads();
     const u128 t = prefix_of(*w.st);
     unsigned long long n = 0;
@@ -380,14 +395,14 @@ __global__ void __launch_bounds__(PP_THREADS) pp_clear_kernel(const Params P, ui
         ++n;
         const uint64_t xm = user_x(P, x, i);
         if (!xm) continue;
-        add_consumption<LAYOUT>(P, xm, i, sR, nullptr);
+        add_consumption<LAYOUT>(P, xm, i, sR, 0, nullptr);
         for (int q = 0; q < P.W; ++q) x[i * P.W + q] = 0u;
     }
     for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
     if ((threadIdx.x & 31) == 0 && n) atomicAdd(&w.st->count, n);
     __syncthreads();
     for (int k = threadIdx.x; k < P.K; k += blockDim.x) {
-        const unsigned long long v = sR[k];
+        const unsigned long long v = sR.get(k);
         if (v) atomicAdd(&w.removed[k], v);
     }
 }
@@ -443,12 +458,25 @@ kp_status kp_postprocess(kp_problem *h, const double *lambda, uint32_t *x_bits, 
     const int levels = (T + PP_MIN_DBITS - 1) / PP_MIN_DBITS;
     const size_t words = (size_t)P.N * 3 + (size_t)bin_words + 3 * (size_t)K + ((size_t)K + 1) / 2 +
                          sizeof(PPState) / 8;
-    unsigned long long *buf = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&buf, words * sizeof(unsigned long long), st);
-    if (e != cudaSuccess) {
-        kp::set_last_error(cudaGetErrorString(e));
-        return e == cudaErrorMemoryAllocation ? KP_ENOMEM : KP_ECUDA;
+    // the keys and lists (24 N bytes) stay with the handle after the first call
+    cudaError_t e = cudaSuccess;
+    if (h->ppwords < words) {
+        if (h->ppbuf) {
+            e = cudaStreamSynchronize(st);  // the previous scratch may still be in use
+            if (e == cudaSuccess) e = cudaFree(h->ppbuf);
+            h->ppbuf = nullptr;
+            h->ppwords = 0;
+        }
+        void *p = nullptr;
+        if (e == cudaSuccess) e = cudaMalloc(&p, words * sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            kp::set_last_error(cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? KP_ENOMEM : KP_ECUDA;
+        }
+        h->ppbuf = static_cast<unsigned long long *>(p);
+        h->ppwords = words;
     }
+    unsigned long long *buf = h->ppbuf;
     PPWork w;
     w.ukey = buf;
     w.list[0] = (int64_t *)(buf + P.N);
@@ -496,8 +524,6 @@ kp_status kp_postprocess(kp_problem *h, const double *lambda, uint32_t *x_bits, 
             e = cudaGetLastError();
         }
     }
-    const cudaError_t ef = cudaFreeAsync(buf, st);
-    if (e == cudaSuccess) e = ef;
     if (e != cudaSuccess) {
         kp::set_last_error(cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? KP_ENOMEM : KP_ECUDA;
