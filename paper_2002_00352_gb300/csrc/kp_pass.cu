@@ -12,7 +12,7 @@
 //                threshold (Sec. 5.2 centres its buckets at lambda_k^t), with
 //                the breakpoints inside the window buffered.  A knapsack one
 //                item of the user touches has a closed-form breakpoint; two
-//                items: pair_sweep in a block-wide sweep phase; three or more:
+//                items: pair_sweep from a per-warp queue; three or more:
 //                rare_kernel (a launch of its own).
 //   MODE_REFINE  Algorithm 4's Map restricted to the key ranges still
 //                unresolved by the threshold selection.
@@ -280,7 +280,8 @@ __device__ __forceinline__ float pick(const float (&a)[N], int j) {
 // checked at creation).  Entries whose knapsack is also consumed by another
 // item of the same user are marked once at creation (Scratch::shmask); all
 // other entries get the closed-form breakpoint in one uniform loop; knapsacks
-// two items share get a pair sweep in the block's sweep phase, those three or
+// two items share get a pair sweep (per-warp queues; per-thread rows swept after
+// every tile when the queues do not fit), those three or
 // more share are left to rare_kernel.
 // ------------------------------------------------------------------------------------------
 template <int THREADS>
