@@ -433,9 +433,12 @@ __device__ __forceinline__ void exchange_sweep(const float (&w)[MAXM], uint32_t 
 // no full set on its path, at its zero crossing; fixed lines never re-enter
 // and a moving line leaves only when overtaken, so the events are few (the
 // loop bound is a guard).  Each event emits (lambda_k, consumption increase).
+// The events come in decreasing lambda_k; the sweep ends at the first one
+// below `stop`, a value at or below the pass's floor (the sink drops that
+// event and every later one).
 template <int MAXM, class Sink>
 __device__ void live_sweep(const float *w, uint64_t SF, int nj, const int *it, const float *sl, float lamk,
-                           const Tree &t, int k, Sink &sink) {
+                           float stop, const Tree &t, int k, Sink &sink) {
     float A[MAXM];
     uint64_t Jm = 0ull, live = 0ull, inq = 0ull;  // items of the live lines; slot masks
     for (int q = 0; q < nj; ++q) {
@@ -502,7 +505,7 @@ __device__ void live_sweep(const float *w, uint64_t SF, int nj, const int *it, c
                 bv2 = v2;
             }
         }
-        if (bq < 0) break;
+        if (bq < 0 || be < stop) break;
         S = (S & ~brem) | (1ull << it[bq]);
         inq = (inq & ~bout) | (1ull << bq);
         cur = be;

@@ -1298,7 +1298,7 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
             auto run = [&](auto &sink) {
                 Walk wf;
                 greedy_walk(ptu, 1, fixedpos, P.tree, wf);  // selection among the fixed lines
-                live_sweep<MAXM>(ptu, wf.sel, nj, it, sl, lamk, P.tree, k, sink);
+                live_sweep<MAXM>(ptu, wf.sel, nj, it, sl, lamk, lamk + tk, P.tree, k, sink);
             };
             if (MODE == MODE_HIST) {
                 WindowSink ws = make_window_sink(P, S, L, smem);
