@@ -419,6 +419,39 @@ __device__ __forceinline__ void exchange_sweep(const float (&w)[MAXM], uint32_t 
     }
 }
 
+// Shortcut of live_sweep below (same arguments, same events): let H = the
+// live lines whose zero crossing z is positive and at or above `stop`, R = the
+// other live lines positive at lambda_k^t.  If every set l holds
+// |SF ∩ l| + |H ∩ l| + [R meets l] <= C_l, no set on the path of a line of H
+// is full when it enters and no set on the path of a line of R ever is: the
+// lines of H enter at their zero crossings in decreasing order, a line of R
+// at its own zero crossing (below `stop`), so the events are exactly
+// (z_q, b_q) for q in H.  Returns false, emitting nothing, when the test fails.
+template <int MAXM, class Sink>
+__device__ __forceinline__ bool live_shortcut(const float *w, uint64_t SF, int nj, const int *it, const float *sl,
+                                              float lamk, float stop, const Tree &t, int k, Sink &sink) {
+    uint64_t Hm = 0ull, Rm = 0ull;  // items of H and R
+    for (int q = 0; q < nj; ++q) {
+        const float A = fmaf(lamk, sl[q], w[it[q]]);
+        if (A > 0.f) {
+            const float z = __fdividef(A, sl[q]);
+            if (z > 0.f && z >= stop)
+                Hm |= 1ull << it[q];
+            else
+                Rm |= 1ull << it[q];
+        }
+    }
+    bool fits = true;
+    for (int l = 0; l < t.L; ++l) {
+        const uint64_t I = t.items[l];
+        fits = fits && (__popcll(SF & I) + __popcll(Hm & I) + ((Rm & I) ? 1 : 0) <= (int)t.cap[l]);
+    }
+    if (!fits) return false;
+    for (int q = 0; q < nj; ++q)
+        if ((Hm >> it[q]) & 1ull) sink.emit_rel(k, __fdividef(fmaf(lamk, sl[q], w[it[q]]), sl[q]), sl[q]);
+    return true;
+}
+
 // Map of Algorithm 4 for one (user, k) over the live moving lines only, in
 // exchange form, for rows of up to 64 items (dense b).  The live lines (slots
 // q < nj, in item order: item it[q], slope sl[q] = b_jk > 0) are the moving
@@ -457,6 +490,9 @@ __device__ void live_sweep(const float *w, uint64_t SF, int nj, const int *it, c
         int bq = -1;
         uint64_t brem = 0ull, bout = 0ull;
         uint64_t cand = live & ~inq;
+        int cl = -1;           // circuit level whose weakest fixed member is cached
+        float cw = FLT_MAX;
+        uint64_t cyb = 0ull;
         while (cand) {
             const int q = __ffsll((long long)cand) - 1;
             cand &= cand - 1;
@@ -466,21 +502,26 @@ __device__ void live_sweep(const float *w, uint64_t SF, int nj, const int *it, c
             if (!fm) {
                 e = __fdividef(A[q], sl[q]);  // zero crossing, nothing to replace
             } else {
-                const uint64_t Cm = S & t.items[__ffs(fm) - 1];
-                uint64_t CF = Cm & ~Jm;
-                float wmin = FLT_MAX;  // weakest fixed member (ties: the higher index is weaker)
-                uint64_t yb = 0ull;
-                while (CF) {
-                    const int j = __ffsll((long long)CF) - 1;
-                    CF &= CF - 1;
-                    const float v = w[j];
-                    if (v <= wmin) {
-                        wmin = v;
-                        yb = 1ull << j;
+                const int lv = __ffs(fm) - 1;
+                const uint64_t Cm = S & t.items[lv];
+                if (lv != cl) {
+                    // weakest fixed member of the circuit (ties: the higher index is weaker)
+                    uint64_t CF = Cm & ~Jm;
+                    cw = FLT_MAX;
+                    cyb = 0ull;
+                    while (CF) {
+                        const int j = __ffsll((long long)CF) - 1;
+                        CF &= CF - 1;
+                        const float v = w[j];
+                        if (v <= cw) {
+                            cw = v;
+                            cyb = 1ull << j;
+                        }
                     }
+                    cl = lv;
                 }
-                e = yb ? __fdividef(A[q] - wmin, sl[q]) : -1.f;
-                rem = yb;
+                e = cyb ? __fdividef(A[q] - cw, sl[q]) : -1.f;
+                rem = cyb;
                 uint64_t mv = inq;  // selected moving members with a smaller slope
                 while (mv) {
                     const int r = __ffsll((long long)mv) - 1;

@@ -34,8 +34,13 @@ namespace {
 constexpr int DENSE_TILE_BYTES = 64 * 1024;   // dense b tile
 
 struct SmemLayout {
-    size_t lamf, kinfo, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, total;
+    size_t lamf, kinfo, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, dq, total;
 };
+
+// Per-warp ring of the dense (user, knapsack) tasks whose sweep the shortcut
+// does not settle: fewer than 32 wait after each round, 32 more can arrive.
+constexpr int DQ_TASKS = 64;
+constexpr int DQ_INPLACE = 16;  // lanes of a round from which the sweeps run in place
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -78,7 +83,7 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
         // ring of WQ_TASKS tasks (regular rows, sets == 0)
         if (mode != MODE_STATE && maxm <= 16)
             o = align16(o + (sets == 0 ? (size_t)(threads / 32) * wq_bytes(maxm) : 2 * 4 * (size_t)threads * maxm));
-        s.tile_p = s.tile_b = s.selm = o;
+        s.tile_p = s.tile_b = s.selm = s.dq = o;
     } else {
         s.tile_p = o;
         o = align16(o + 4 * (size_t)T * M);
@@ -86,6 +91,8 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
         o = align16(o + 4 * (size_t)T * M);
         s.selm = o;
         o = align16(o + 8 * (size_t)T);
+        s.dq = o;
+        if (mode != MODE_STATE) o = align16(o + 4 * (size_t)(threads / 32) * DQ_TASKS);
         s.tile_b = o;
         o = align16(o + 4 * (size_t)T * M * K);
     }
@@ -1218,6 +1225,44 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
     const int du = THREADS / K, dk = THREADS - du * K;
     int u = threadIdx.x / K, k = threadIdx.x - u * K;
     const float4 *kinfo = (const float4 *)(smem + L.kinfo);
+    const unsigned lane = threadIdx.x & 31u;
+    uint32_t *dq = (uint32_t *)(smem + L.dq) + (threadIdx.x >> 5) * DQ_TASKS;
+    int qh = 0, qn = 0;  // the warp's ring: head, count
+    // the full sweep of a queued task (task = u K + k), its lines found again
+    // from the tile exactly as in the first visit
+    auto slow_task = [&](uint32_t task) {
+        const int su = (int)(task / (uint32_t)K), sk = (int)(task - (uint32_t)su * (uint32_t)K);
+        const float *bc = tb + (size_t)su * M * K + sk;
+        const float *pu = pt + (size_t)su * M;
+        const float lk = lamf[sk];
+        const float t = kinfo[sk].w;
+        int it[MAXM];
+        float sl[MAXM];
+        int n = 0;
+        uint64_t fp = 0ull;
+        for (int j = 0; j < M; ++j) {
+            const float b = bc[(size_t)j * K];
+            const float wj = pu[j];
+            if (b > 0.f) {
+                if (wj >= t * b) {
+                    it[n] = j;
+                    sl[n] = b;
+                    ++n;
+                }
+            } else if (wj > 0.f) {
+                fp |= 1ull << j;
+            }
+        }
+        Walk wf;
+        greedy_walk(pu, 1, fp, P.tree, wf);
+        if (MODE == MODE_HIST) {
+            WindowSink ws = make_window_sink(P, S, L, smem);
+            live_sweep<MAXM>(pu, wf.sel, n, it, sl, lk, lk + t, P.tree, sk, ws);
+        } else {
+            RefineSink rs = make_refine_sink(P, S, L, smem);
+            live_sweep<MAXM>(pu, wf.sel, n, it, sl, lk, lk + t, P.tree, sk, rs);
+        }
+    };
     // every lane takes the same number of rounds (the tasks' loops have
     // data-dependent trip counts: the warp meets again after each task)
     for (int base = 0; base < nu * K; base += THREADS, u += du, k += dk) {
@@ -1225,6 +1270,11 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
             k -= K;
             ++u;
         }
+        bool slow = false;
+        int it[MAXM];     // the task's live lines (item, slope) and the
+        float sl[MAXM];   // selection among its fixed lines, kept for a
+        int nj = 0;       // sweep in place
+        uint64_t sfsel = 0ull;
         if (u < nu) {
         const float *bcol = tb + (size_t)u * M * K + k;
         const float *ptu = pt + (size_t)u * M;
@@ -1283,32 +1333,59 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
             }
         }
         if (MODE != MODE_STATE && livem) {
-            const int nj = __popcll(livem);
-            int it[MAXM];
-            float sl[MAXM];
-            int n = 0;
             uint64_t q = livem;
             while (q) {
                 const int j = __ffsll((long long)q) - 1;
                 q &= q - 1;
-                it[n] = j;
-                sl[n] = bcol[(size_t)j * K];
-                ++n;
+                it[nj] = j;
+                sl[nj] = bcol[(size_t)j * K];
+                ++nj;
             }
-            auto run = [&](auto &sink) {
-                Walk wf;
-                greedy_walk(ptu, 1, fixedpos, P.tree, wf);  // selection among the fixed lines
-                live_sweep<MAXM>(ptu, wf.sel, nj, it, sl, lamk, lamk + tk, P.tree, k, sink);
-            };
+            Walk wf;
+            greedy_walk(ptu, 1, fixedpos, P.tree, wf);  // selection among the fixed lines
+            sfsel = wf.sel;
             if (MODE == MODE_HIST) {
                 WindowSink ws = make_window_sink(P, S, L, smem);
-                run(ws);
+                slow = !live_shortcut<MAXM>(ptu, sfsel, nj, it, sl, lamk, lamk + tk, P.tree, k, ws);
             } else {
                 RefineSink rs = make_refine_sink(P, S, L, smem);
-                run(rs);
+                slow = !live_shortcut<MAXM>(ptu, sfsel, nj, it, sl, lamk, lamk + tk, P.tree, k, rs);
             }
         }
         }
+        if (MODE != MODE_STATE) {
+            // tasks the shortcut did not settle: with most lanes of the round
+            // among them the full sweep runs in place; otherwise they wait in
+            // the warp's ring and 32 of them at a time run it on all lanes
+            const unsigned bal = __ballot_sync(0xffffffffu, slow);
+            if (__popc(bal) >= DQ_INPLACE) {
+                if (slow) {
+                    const float lk = lamf[k];
+                    const float *pu = pt + (size_t)u * M;
+                    if (MODE == MODE_HIST) {
+                        WindowSink ws = make_window_sink(P, S, L, smem);
+                        live_sweep<MAXM>(pu, sfsel, nj, it, sl, lk, lk + kinfo[k].w, P.tree, k, ws);
+                    } else {
+                        RefineSink rs = make_refine_sink(P, S, L, smem);
+                        live_sweep<MAXM>(pu, sfsel, nj, it, sl, lk, lk + kinfo[k].w, P.tree, k, rs);
+                    }
+                }
+            } else if (bal) {
+                if (slow) dq[(qh + qn + __popc(bal & ((1u << lane) - 1u))) & (DQ_TASKS - 1)] = (uint32_t)(u * K + k);
+                qn += __popc(bal);
+                __syncwarp();
+                if (qn >= 32) {
+                    const uint32_t task = dq[(qh + (int)lane) & (DQ_TASKS - 1)];
+                    qh = (qh + 32) & (DQ_TASKS - 1);
+                    qn -= 32;
+                    slow_task(task);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (MODE != MODE_STATE && qn > 0) {
+        if ((int)lane < qn) slow_task(dq[(qh + (int)lane) & (DQ_TASKS - 1)]);
         __syncwarp();
     }
     __syncthreads();
