@@ -450,6 +450,36 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
     }
 }
 
+// Algorithm 1 in its literal bottom-up form over the candidates cand (items
+// with p~ > 0): beats[j] is the set of items ranked before j (larger p~, ties
+// to the lower index); at set S_l (deepest first) an item survives if fewer
+// than C_l survivors of S_l rank before it.  Registers only (M <= 16).
+template <int MAXM>
+__device__ __forceinline__ uint32_t greedy_ranked(const float *pt, uint32_t cand, const Tree &T) {
+    uint32_t beats[MAXM];
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) beats[j] = 0u;
+#pragma unroll
+    for (int j = 1; j < MAXM; ++j)
+#pragma unroll
+        for (int j2 = 0; j2 < j; ++j2) {
+            const bool first = pt[j2] >= pt[j];  // j2 < j wins ties
+            beats[j] |= first ? (1u << j2) : 0u;
+            beats[j2] |= first ? 0u : (1u << j);
+        }
+    uint32_t G = cand;
+    for (int l = 0; l < T.L; ++l) {
+        const uint32_t inl = G & (uint32_t)T.items[l];
+        const int cap = T.cap[l];
+        uint32_t drop = 0u;
+#pragma unroll
+        for (int j = 0; j < MAXM; ++j)
+            if (((inl >> j) & 1u) && __popc(beats[j] & inl) >= cap) drop |= 1u << j;
+        G &= ~drop;
+    }
+    return G;
+}
+
 // Lean per-user routine for M <= MAXM <= 16 and at most 32 entries: reduced
 // costs, decisions and margins live in registers, loops run over the items in
 // compile-time order with predication, so the lanes of a warp stay together.
@@ -457,12 +487,10 @@ __device__ __noinline__ void csr_user(const Params &P, const Scratch &S, int64_t
 // of the user belongs to item e / C and all entry loops unroll; with
 // P.vec the user's rows are read with vector loads.  C = 0: counts are read
 // from csr_item_nnz.
-//   Algorithm 1 is evaluated in its literal bottom-up form: beats[j] is the set
-//   of items ranked before j (larger p~, ties to the lower index); at set S_l
-//   an item survives if fewer than C_l survivors of S_l rank before it.
+//   Algorithm 1 is evaluated in its literal bottom-up form (greedy_ranked).
 // Returns the user's list of knapsacks that exactly two of its items use
-// (shmask.y: they need a pair sweep); the user's p~ row and rank masks are
-// then left in prow (and the row after it).
+// (shmask.y: they need a pair sweep); the user's p~ row and positive items
+// are then left in prow (and the row after it).
 template <int MAXM, int C, int MODE, class Sink>
 __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch &S, int64_t i,
                                                   int64_t e0, const float *lamf, const float4 *kinfo,
@@ -557,32 +585,17 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
             pt[j] = acc;
         }
     }
-    // Algorithm 1
-    uint32_t beats[MAXM];
+    // Algorithm 1.  A set holding no more positive items than its cap drops
+    // none (and neither does any set after it), so the rank masks and the
+    // set loop run only for users with some set over its cap.
     uint32_t pos = 0;
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-        beats[j] = 0u;
+    for (int j = 0; j < MAXM; ++j)
         if (j < M && pt[j] > 0.f) pos |= 1u << j;
-    }
-#pragma unroll
-    for (int j = 1; j < MAXM; ++j)
-#pragma unroll
-        for (int j2 = 0; j2 < j; ++j2) {
-            const bool first = pt[j2] >= pt[j];  // j2 < j wins ties
-            beats[j] |= first ? (1u << j2) : 0u;
-            beats[j2] |= first ? 0u : (1u << j);
-        }
     uint32_t G = pos;
-    for (int l = 0; l < T.L; ++l) {
-        const uint32_t inl = G & (uint32_t)T.items[l];
-        const int cap = T.cap[l];
-        uint32_t drop = 0u;
-#pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-            if (((inl >> j) & 1u) && __popc(beats[j] & inl) >= cap) drop |= 1u << j;
-        G &= ~drop;
-    }
+    bool over = false;
+    for (int l = 0; l < T.L; ++l) over = over || __popc(pos & (uint32_t)T.items[l]) > (int)T.cap[l];
+    if (over) G = greedy_ranked<MAXM>(pt, pos, T);
     uint32_t full = 0u;
     for (int l = 0; l < T.L; ++l)
         if (__popc(G & (uint32_t)T.items[l]) >= (int)T.cap[l]) full |= 1u << l;
@@ -618,33 +631,39 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
     if constexpr (MODE == MODE_STATE) {
         return 0u;
     } else {
-        // exchange thresholds theta_j and margins p~_j - theta_j, without
-        // data-dependent branches: ts_j = max over the sets on j's path of
-        // their best rejected item whose deepest full set it is (j selected),
-        // tn_j = the weakest selected item of j's deepest full set
+        // exchange thresholds theta_j and margins p~_j - theta_j: ts_j = max
+        // over the sets on j's path of their best rejected item whose deepest
+        // full set it is (j selected), tn_j = the weakest selected item of j's
+        // deepest full set.  Only full sets contribute, so the loop visits the
+        // full sets, deepest first: the items whose deepest full set is l are
+        // those of l that no set visited before holds.
         const uint32_t rej = pos & ~G;
-        int dy[MAXM];
         float ts[MAXM], tn[MAXM];
 #pragma unroll
         for (int y = 0; y < MAXM; ++y) {
-            dy[y] = __ffs(T.ipath[y] & full) - 1;
             ts[y] = 0.f;
             tn[y] = 0.f;
         }
-        for (int l = 0; l < T.L; ++l) {
-            const uint32_t selL = G & (uint32_t)T.items[l];
+        uint32_t fl = full, cov = 0u;
+        while (fl) {
+            const int l = __ffs(fl) - 1;
+            fl &= fl - 1;
+            const uint32_t I = (uint32_t)T.items[l];
+            const uint32_t selL = G & I, dyl = I & ~cov, rl = rej & dyl;
+            cov |= I;
             float mn = FLT_MAX, mx = 0.f;
 #pragma unroll
             for (int j = 0; j < MAXM; ++j) {
                 mn = ((selL >> j) & 1u) ? fminf(mn, pt[j]) : mn;
-                mx = (((rej >> j) & 1u) && dy[j] == l) ? fmaxf(mx, pt[j]) : mx;
+                mx = ((rl >> j) & 1u) ? fmaxf(mx, pt[j]) : mx;
             }
 #pragma unroll
             for (int j = 0; j < MAXM; ++j) {
-                ts[j] = ((T.ipath[j] >> l) & 1u) ? fmaxf(ts[j], mx) : ts[j];
-                tn[j] = dy[j] == l ? mn : tn[j];
+                ts[j] = ((I >> j) & 1u) ? fmaxf(ts[j], mx) : ts[j];
+                tn[j] = ((dyl >> j) & 1u) ? mn : tn[j];
             }
         }
+        __syncwarp(wmask);
         float mg[MAXM];
 #pragma unroll
         for (int j = 0; j < MAXM; ++j) mg[j] = pt[j] - (((G >> j) & 1u) ? ts[j] : tn[j]);
@@ -736,12 +755,8 @@ __device__ __forceinline__ uint32_t csr_user_fast(const Params &P, const Scratch
         }
         if (pending) {
 #pragma unroll
-            for (int j = 0; j < MAXM; ++j) {
-                prow[j] = pt[j];
-                // rank masks use bits 0..15 (M <= 16); the positive items ride in
-                // the high half of the first word
-                brow[j] = beats[j] | (j == 0 ? pos << 16 : 0u);
-            }
+            for (int j = 0; j < MAXM; ++j) prow[j] = pt[j];
+            brow[0] = pos;  // the sweep ranks the items again where a cap needs it
         }
         return pending;
     }
@@ -773,22 +788,17 @@ __device__ __forceinline__ void sweep_task(const Params &P, const float4 *kinfo,
         ib = j2;
     }
     const uint32_t J = (1u << ia) | (1u << ib);
-    static_assert(MAXM <= 16, "rank masks and the positive items share a word");
-    uint32_t bt[MAXM];
-#pragma unroll
-    for (int j2 = 0; j2 < MAXM; ++j2) bt[j2] = brow[j2] & 0xffffu;
-    const uint32_t pos = brow[0] >> 16;
-    // selection among the fixed lines: Algorithm 1 over pos minus J with the
-    // owner's rank masks
+    const uint32_t pos = brow[0];
+    // selection among the fixed lines: Algorithm 1 over pos minus J (ranked
+    // only where a set holds more of them than its cap)
     uint32_t SF = pos & ~J;
-    for (int l = 0; l < T.L; ++l) {
-        const uint32_t inl = SF & (uint32_t)T.items[l];
-        const int cap = T.cap[l];
-        uint32_t drop = 0u;
+    bool over = false;
+    for (int l = 0; l < T.L; ++l) over = over || __popc(SF & (uint32_t)T.items[l]) > (int)T.cap[l];
+    if (over) {
+        float w[MAXM];
 #pragma unroll
-        for (int j = 0; j < MAXM; ++j)
-            if (((inl >> j) & 1u) && __popc(bt[j] & inl) >= cap) drop |= 1u << j;
-        SF &= ~drop;
+        for (int j = 0; j < MAXM; ++j) w[j] = prow[j];
+        SF = greedy_ranked<MAXM>(w, SF, T);
     }
     pair_sweep(prow, SF, ia, sa, ib, sb, kinfo[k], T, k, sink);
 }
