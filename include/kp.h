@@ -182,6 +182,29 @@ kp_status kp_scd_step(kp_problem *h, const double *lambda, double *lambda_next, 
 kp_status kp_bcd_step(kp_problem *h, const double *lambda, const uint8_t *block, double *lambda_next,
                       double *dual_sum, double *primal_sum, void *stream);
 
+/* One iteration of Algorithm 4 whose Reduce is the bucketing with
+ * interpolation of Sec. 5.2 (an approximation of the exact Reduce above).
+ * Every breakpoint v of knapsack k goes to the bucket
+ *   id(v) = 0 if |v - lambda_k| < Delta_k,
+ *           else sign(v - lambda_k) (1 + floor(log2(|v - lambda_k| / Delta_k)))
+ * (narrowest at lambda_k = lambda_k^t, doubling away from it; clamped to
+ * [-127, 127]; computed in FP32 from the FP32 breakpoint, lambda_k rounded
+ * to FP32 and Delta_k), with Delta_k = delta * lambda_k, or delta where
+ * lambda_k = 0.  Walking down from the highest bucket, the first bucket
+ * whose mass takes the cumulative mass above B_k holds lambda_next_k; inside
+ * it the mass is taken as uniform over the bucket's range
+ *   id 0: [lambda_k - Delta_k, lambda_k + Delta_k),
+ *   id > 0: [lambda_k + Delta_k 2^(id-1), lambda_k + Delta_k 2^id),
+ *   id < 0: [lambda_k - Delta_k 2^|id|, lambda_k - Delta_k 2^(|id|-1)),
+ * and lambda_next_k is the point where the cumulative mass reaches B_k
+ * (clamped to the bucket and to >= 0); lambda_next_k = 0 when the whole
+ * emitted mass is within B_k.  Bucket masses are exact fixed-point sums.
+ * One user pass per call, no re-run passes.  lambda, lambda_next: device
+ * FP64 [K], must not alias.  KP_EINVAL for delta outside (0, 1e30].  Leaves
+ * the exact Reduce's threshold prediction untouched. */
+kp_status kp_scd_step_bucketed(kp_problem *h, const double *lambda, double delta, double *lambda_next,
+                               void *stream);
+
 /* Gradient of the dual g(lambda, p, B) of Eq. (5) by Danskin's theorem at the
  * maximiser x* (from kp_solve_users / kp_reduce_consumption at the same
  * lambda), each scaled by the device float64 scalar *upstream:
@@ -276,15 +299,32 @@ kp_status kp_reduce_consumption_noalloc(const kp_desc *desc, const double *lambd
 
 /* Autotuner: times the breakpoint pass of a dense instance on its first
  * min(N, 2^18) users at several tile sizes (users staged per shared-memory
- * tile: the default, 8, 16, 32, 64, 128, 256 where they fit) and keeps the
- * fastest for every later call on the handle; *chosen (may be NULL) receives
- * it.  A CSR instance has no run-time tile size (*chosen = 0).  Synchronous;
+ * tile: the default, 8, 16, 32, 64, 128, 256 where they fit) in both staging
+ * modes (kp_set_tile) and keeps the fastest pair for every later call on the
+ * handle; *chosen (may be NULL) receives the tile size.  KP_ETIMEOUT if a
+ * timed pass reported one.  A CSR instance has no run-time tile size (*chosen = 0).  Synchronous;
  * allocates K doubles for the duration of the call.  (Not in the paper.) */
 kp_status kp_autotune(kp_problem *h, int32_t *chosen, void *stream);
 
+/* Dense instances: the users per shared-memory tile (1 .. the default, which
+ * fills a 64 KB tile of b; 0 = the default) and the staging mode of the user
+ * passes:
+ * 0 = each tile loaded by the block's threads, then computed (two blocks per
+ * SM overlap one's loads with the other's work); 1 = two buffers of half a
+ * tile each, the next tile's p and b brought in by 1-D bulk asynchronous
+ * copies (cp.async.bulk, completion on an mbarrier, waits bounded at 2 s:
+ * KP_ETIMEOUT in kp_device_status) while the current one is computed; used
+ * when p and b are 16-byte aligned and half a tile holds at least 4 users,
+ * otherwise mode 0.  Results do not depend on either choice.  KP_EINVAL for
+ * a CSR instance or values out of range.  (Not in the paper.) */
+kp_status kp_set_tile(kp_problem *h, int32_t users, int32_t staging);
+
 /* Synchronises the stream and returns the device-side status accumulated by
  * the handle's kernels since the last call (KP_OK, KP_ETIMEOUT or
- * KP_ESTATE), then clears it. */
+ * KP_ESTATE), then clears it.  KP_ETIMEOUT: a dense user pass waited more
+ * than 2 s for the bulk asynchronous copy of a tile of users into shared
+ * memory (the block then stops, after waiting for its copies in flight; the
+ * pass's results are incomplete). */
 kp_status kp_device_status(kp_problem *h, void *stream);
 
 /* Counters of the last kp_threshold_select on this handle (device values,

@@ -10,8 +10,9 @@ routine per step of the paper: Sec. 4.2 and Algorithm 1 for the per-user
 greedy, Eq. (14) and Algorithm 2 for dual descent, Algorithms 3-4 for
 synchronous coordinate descent, Algorithm 5 for its one-item-per-knapsack
 special case, Sec. 5.4 for post-processing).  This module
-only marshals numpy arrays into those routines and converts the CSR storage of
-``b`` into the dense layout the oracle reads.
+marshals numpy arrays into those routines and converts the CSR storage of
+``b`` into the dense layout the oracle reads; the bucketed Reduce of Sec. 5.2
+(bucket_ids ... bucket_step), a few lines over the emitted pairs, is numpy.
 """
 from __future__ import annotations
 
@@ -243,6 +244,79 @@ def bcd_step(p, b, S, C, lam, B, block):
     nxt, _, _ = scd_step(p, b, S, C, lam, B)
     block = np.asarray(block, dtype=bool)
     return np.where(block, nxt, lam)
+
+
+def bucket_ids(v1, lam_k, delta_k) -> np.ndarray:
+    """Sec. 5.2 bucket of each candidate v1 around lam_k (reading of the bucket
+    formula: id 0 where |d| < Delta, else sign(d) (1 + floor(log2(|d| / Delta))),
+    d = v1 - lam_k, clamped to [-127, 127]).  The id is an integer decided by
+    floating point, so it is taken in the precision of the kernel: v1, lam_k and
+    Delta rounded to FP32, d and |d| / Delta rounded to FP32 (numpy float32
+    arithmetic is IEEE round-to-nearest), floor(log2) exact from frexp."""
+    v = np.asarray(v1, dtype=np.float64).astype(np.float32)
+    lt = np.float32(lam_k)
+    dl = np.float32(delta_k)
+    d = (v - lt).astype(np.float32)
+    with np.errstate(over="ignore"):  # overflow to inf is part of the definition (clamped)
+        a = (np.abs(d) / dl).astype(np.float32)
+    ids = np.zeros(v.shape, dtype=np.int64)
+    big = a >= np.float32(1.0)
+    _, e = np.frexp(a[big])  # a = m 2^e with m in [0.5, 1): 1 + floor(log2 a) = e
+    e = np.where(np.isinf(a[big]), 127, e).astype(np.int64)
+    e = np.minimum(e, 127)
+    ids[big] = np.where(d[big] < 0, -e, e)
+    return ids
+
+
+def bucket_delta(lam_k, delta) -> np.float32:
+    """Delta_k of a bucketed step: delta * lam_k (delta where lam_k = 0), in FP32,
+    at least the smallest normal FP32 value."""
+    dl = np.float32(delta * lam_k if lam_k > 0 else delta)
+    return max(dl, np.finfo(np.float32).tiny)
+
+
+def bucket_range(id_, lam_k, delta_k):
+    """[lo, hi) of bucket id_ (FP64 from the FP32 lam_k and Delta_k)."""
+    lt, dl = float(np.float32(lam_k)), float(np.float32(delta_k))
+    if id_ == 0:
+        return lt - dl, lt + dl
+    if id_ > 0:
+        return lt + dl * 2.0 ** (id_ - 1), lt + dl * 2.0 ** id_
+    return lt - dl * 2.0 ** (-id_), lt - dl * 2.0 ** (-id_ - 1)
+
+
+def bucket_reduce(v1, v2, Bk, lam_k, delta_k, ids=None) -> float:
+    """Sec. 5.2 Reduce for one knapsack: bucket the candidates around lam_k, sum
+    v2 per bucket, walk down from the highest bucket to the first one whose mass
+    takes the cumulative mass above Bk, and interpolate linearly inside it (its
+    mass taken as uniform over its range); 0 if the whole mass is within Bk
+    (Algorithm 4).  ids: the candidates' buckets if already known."""
+    v2 = np.asarray(v2, dtype=np.float64)
+    if ids is None:
+        ids = bucket_ids(v1, lam_k, delta_k)
+    mass = np.zeros(256)
+    np.add.at(mass, np.asarray(ids) + 128, v2)
+    A = 0.0
+    for b in range(255, 0, -1):
+        if A + mass[b] > Bk:
+            lo, hi = bucket_range(b - 128, lam_k, delta_k)
+            f = (Bk - A) / mass[b]
+            lam = min(max(hi - f * (hi - lo), lo), hi)
+            return max(lam, 0.0)
+        A += mass[b]
+    return 0.0
+
+
+def bucket_step(p, b, S, C, lam, B, delta):
+    """One Algorithm 4 iteration with the Sec. 5.2 bucketed Reduce: the Map at lam
+    (scd_map_users), then bucket_reduce per knapsack with Delta_k = bucket_delta."""
+    lam, B = _f64(lam), _f64(B)
+    _, ek, v1, v2 = scd_map_users(p, b, S, C, lam)
+    out = np.zeros(len(lam))
+    for k in range(len(lam)):
+        sel = ek == k
+        out[k] = bucket_reduce(v1[sel], v2[sel], B[k], lam[k], bucket_delta(lam[k], delta))
+    return out
 
 
 def presolve(p, b, S, C, B, users, iters):

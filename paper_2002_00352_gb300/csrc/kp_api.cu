@@ -202,6 +202,7 @@ kp_status fill_params(const kp_desc *d, kp::Params &P, uint32_t *flags, cudaStre
     if (so < 0) so = 0;
     P.fixo = so;
     P.tile = P.layout == KP_B_DENSE ? kp::dense_tile_users(P) : 0;
+    P.stage = 0;
     return KP_OK;
 }
 
@@ -422,6 +423,20 @@ kp_status kp_bcd_step(kp_problem *h, const double *lambda, const uint8_t *block,
     return s;
 }
 
+kp_status kp_scd_step_bucketed(kp_problem *h, const double *lambda, double delta, double *lambda_next,
+                               void *stream) {
+    if (!check_handle(h) || !lambda || !lambda_next) return fail(KP_EINVAL, "kp_scd_step_bucketed: NULL argument");
+    if (lambda == lambda_next) return fail(KP_EINVAL, "kp_scd_step_bucketed: lambda_next must not alias lambda");
+    if (!(delta > 0.0) || !(delta <= 1e30)) return fail(KP_EINVAL, "kp_scd_step_bucketed: delta must be in (0, 1e30]");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = kp::launch_bucket_prep(h->P, h->S, lambda, delta, st);
+    if (e == cudaSuccess)
+        e = kp::launch_user_pass(h->P, h->S, lambda, kp::MODE_REFINE, kp::BUCKET_ROUND, nullptr, st);
+    if (e == cudaSuccess) e = kp::launch_bucket_select(h->P, h->S, lambda, lambda_next, st);
+    if (e != cudaSuccess) return cuda_fail(e, "kp_scd_step_bucketed");
+    return KP_OK;
+}
+
 kp_status kp_dual_backward(kp_problem *h, const double *lambda, const uint32_t *x_bits,
                            const double *R, const double *upstream, double *grad_lambda,
                            float *grad_p, double *grad_B, void *stream) {
@@ -452,12 +467,14 @@ kp_status kp_autotune(kp_problem *h, int32_t *chosen, void *stream) {
     KP_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
     KP_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
     const int def = kp::dense_tile_users(P);
-    int best = def;
+    int best = def, best_stage = 0;
     float best_ms = -1.f;
     const int cands[] = {def, 8, 16, 32, 64, 128, 256};
-    for (int c : cands) {
+    for (int cs = 0; cs < 14; ++cs) {
+        const int c = cands[cs % 7], stage = cs / 7;
         if (c > def && c != def) continue;  // larger tiles than the default do not fit its shared memory budget
         Q.tile = c;
+        Q.stage = stage;
         cudaError_t e = kp::launch_user_pass(Q, h->S, lam, kp::MODE_HIST, 0, nullptr, st);  // warm
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         for (int r = 0; r < 3 && e == cudaSuccess; ++r)
@@ -473,11 +490,15 @@ kp_status kp_autotune(kp_problem *h, int32_t *chosen, void *stream) {
         if (best_ms < 0.f || ms < best_ms) {
             best_ms = ms;
             best = c;
+            best_stage = stage;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(lam);
+    int32_t status = 0;  // a bounded wait that ran out while timing
+    KP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    KP_CUDA(cudaMemcpy(&status, &h->S.ctr->status, 4, cudaMemcpyDeviceToHost), "status copy");
     // the timed passes accumulated into the scratch: clear what the next call consumes
     kp::Scratch &S = h->S;
     KP_CUDA(cudaMemsetAsync(S.Rfix, 0, sizeof(unsigned long long) * P.K, st), "cudaMemsetAsync");
@@ -486,8 +507,22 @@ kp_status kp_autotune(kp_problem *h, int32_t *chosen, void *stream) {
     KP_CUDA(cudaMemsetAsync(S.ovf, 0, sizeof(uint32_t) * P.K, st), "cudaMemsetAsync");
     KP_CUDA(cudaMemsetAsync(S.ctr, 0, sizeof(kp::Counters), st), "cudaMemsetAsync");
     KP_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (status & (1 << KP_ETIMEOUT)) return fail(KP_ETIMEOUT, "kp_autotune: a timed pass's bounded wait ran out");
     P.tile = best;
+    P.stage = best_stage;
     if (chosen) *chosen = best;
+    return KP_OK;
+}
+
+kp_status kp_set_tile(kp_problem *h, int32_t users, int32_t staging) {
+    if (!check_handle(h)) return fail(KP_EINVAL, "kp_set_tile: NULL handle");
+    kp::Params &P = h->P;
+    if (P.layout != KP_B_DENSE) return fail(KP_EINVAL, "kp_set_tile: the instance has no dense tiles");
+    if (users == 0) users = kp::dense_tile_users(P);
+    if (users < 1 || users > kp::dense_tile_users(P) || (staging != 0 && staging != 1))
+        return fail(KP_EINVAL, "kp_set_tile: users must be in 1..%d and staging 0 or 1", kp::dense_tile_users(P));
+    P.tile = users;
+    P.stage = staging;
     return KP_OK;
 }
 

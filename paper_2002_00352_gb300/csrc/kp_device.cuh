@@ -670,6 +670,64 @@ __device__ void sweep_k(const float *pt, int ps, const float *s, int ss, int M, 
 }
 
 // ---------------------------------------------------------------------------
+// bulk asynchronous copies global -> shared (1-D cp.async.bulk, completion
+// counted in bytes on an mbarrier) with bounded waits
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+// the barriers' initialisation made visible to the asynchronous proxy
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// this thread's earlier generic accesses of shared memory ordered before later
+// asynchronous-proxy writes (a buffer refilled after it was read)
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// one arrival that also announces `bytes` of transactions on the barrier
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared memory, completing `bytes` transactions on bar
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(d), "l"(src), "r"(bytes), "r"(b) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of the given parity to complete; false after about
+// limit_ns nanoseconds (or 2^24 polls) without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
 // shared-memory atomics through the shared state space (never generic)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t shared_inc_u32(uint32_t *p) {
@@ -800,10 +858,31 @@ struct WindowSink {
     }
 };
 
+// Bucket of a candidate lambda_k = v around lambda_k^t = lt (Sec. 5.2): with
+// d = v - lt, id 0 for |d| < Delta, else sign(d) (1 + floor(log2(|d| / Delta))),
+// so the buckets are narrowest at lambda_k^t and double away from it; ids are
+// clamped to [-127, 127] and stored at id + 128.  FP32 with IEEE rounding
+// (d and |d| / Delta rounded to nearest), floor(log2) from the exponent field.
+__device__ __forceinline__ int bucket_index(float v, float lt, float delta) {
+    const float d = __fsub_rn(v, lt);
+    const float a = __fdiv_rn(fabsf(d), delta);
+    int id = 0;
+    if (a >= 1.f) {
+        const int e = (int)((__float_as_uint(a) >> 23) & 0xffu) - 127;  // a >= 1: normal or inf
+        id = 1 + e;
+        if (id > 127) id = 127;
+        if (d < 0.f) id = -id;
+    }
+    return id + 128;
+}
+
 // Refine pass: sub-histogram of the unresolved range + buffer of its entries.
+// A knapsack of a bucketed step (shift -1) bins every breakpoint by its
+// bucket around lambda_k^t instead (bucket_index).
 struct RefineSink {
     const uint32_t *lo, *hi;      // [K]; empty range for resolved knapsacks
     const int32_t *shift;         // [K]
+    const float4 *kinfo;          // [K] (shared): lambda_k^t; bucketed step: Delta_k in .y
     unsigned long long *subhist;  // [K][NSUB] global
     uint32_t *bcnt;               // [K] (shared)
     uint2 *buf;
@@ -811,6 +890,12 @@ struct RefineSink {
     float bscale;
     __device__ __forceinline__ void emit(int k, float v1, float v2) {
         if (!(v1 > 0.f) || !(v2 > 0.f)) return;
+        if (shift[k] < 0) {
+            const float4 ki = kinfo[k];
+            atomicAdd(&subhist[(size_t)k * NSUB + bucket_index(v1, ki.x, ki.y)],
+                      (unsigned long long)bmass(v2, bscale));
+            return;
+        }
         const uint32_t key = key_of(v1);
         if (key < lo[k] || key >= hi[k]) return;
         const int sb = (int)((key - lo[k]) >> shift[k]);

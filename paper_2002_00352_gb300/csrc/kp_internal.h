@@ -35,11 +35,12 @@ struct SelK {
     uint32_t wlo, whi;    // window [wlo, whi) used by the last pass
     uint32_t lo, hi;      // unresolved key range [lo, hi)
     unsigned long long above;  // fixed-point mass at or above hi
-    int32_t state;        // 0 resolved, 1 needs a refine pass
+    int32_t state;        // 0 resolved, 1 needs a refine pass, 2 bucketed step (Sec. 5.2)
     uint32_t last_nz_key; // key of the last non-zero lambda_k (centre when lambda_k = 0)
     uint32_t for_key;     // key of the lambda_k the prediction below is for
     uint32_t pred_key;    // predicted key of the next lambda_k (centre of the next pass)
     uint32_t prev_key;    // key of the lambda_k before for_key
+    float bdelta;         // bucket width Delta_k of a bucketed step (state 2)
 };
 
 // global counters (device resident)
@@ -72,6 +73,7 @@ struct Params {
     float bscale;              // 2^fixs: the mass of an entry is round(b * bscale) <= 2^30
     int32_t fixo;              // fixed-point shift of the objective sums
     int32_t tile;              // dense: users per shared-memory tile
+    int32_t stage;             // dense: 0 synchronous tile loads, 1 double-buffered bulk asynchronous copies
     int32_t creg;              // CSR: every item has exactly creg entries (0: not regular)
     int32_t vec;               // CSR regular rows aligned for vector loads (M in {8, 10, 16})
     int64_t uoff0;             // csr_user_off[0]
@@ -159,6 +161,14 @@ int pass_grid_size(const Params &P);
 cudaError_t launch_finalize(const Params &P, const Scratch &S, const double *lambda, double *R,
                             double *dual, double *primal, double *g, double alpha,
                             double *lambda_next, cudaStream_t st);
+// bucketed Reduce (Sec. 5.2): the pass of round BUCKET_ROUND (re-run mode,
+// every knapsack in state 2) bins every breakpoint by its bucket around
+// lambda_k^t; the select interpolates inside the crossing bucket
+constexpr int BUCKET_ROUND = 7;
+cudaError_t launch_bucket_prep(const Params &P, const Scratch &S, const double *lambda, double delta,
+                               cudaStream_t st);
+cudaError_t launch_bucket_select(const Params &P, const Scratch &S, const double *lambda, double *lambda_next,
+                                 cudaStream_t st);
 cudaError_t launch_select(const Params &P, const Scratch &S, const double *lambda,
                           double *lambda_next, int round, cudaStream_t st);
 cudaError_t launch_batch_pass(const BatchDev &B, int maxm, size_t smem, int grid, const double *lam,

@@ -34,7 +34,9 @@ namespace {
 constexpr int DENSE_TILE_BYTES = 64 * 1024;   // dense b tile
 
 struct SmemLayout {
-    size_t lamf, kinfo, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, dq, total;
+    size_t lamf, kinfo, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, dq;
+    size_t tile_p2, tile_b2, bars;  // second stage buffers and their mbarriers (double-buffered pass)
+    size_t total;
 };
 
 // Per-warp ring of the dense (user, knapsack) tasks whose sweep the shortcut
@@ -55,7 +57,7 @@ __host__ __device__ inline size_t wq_bytes(int maxm) {
 }
 
 __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int maxm, int threads,
-                                                  int T, int mode, int sets = 1) {
+                                                  int T, int mode, int sets = 1, int nbuf = 1) {
     SmemLayout s;
     size_t o = 0;
     s.lamf = o;
@@ -84,6 +86,7 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
         if (mode != MODE_STATE && maxm <= 16)
             o = align16(o + (sets == 0 ? (size_t)(threads / 32) * wq_bytes(maxm) : 2 * 4 * (size_t)threads * maxm));
         s.tile_p = s.tile_b = s.selm = s.dq = o;
+        s.tile_p2 = s.tile_b2 = s.bars = o;
     } else {
         s.tile_p = o;
         o = align16(o + 4 * (size_t)T * M);
@@ -95,6 +98,15 @@ __host__ __device__ inline SmemLayout smem_layout(int layout, int K, int M, int 
         if (mode != MODE_STATE) o = align16(o + 4 * (size_t)(threads / 32) * DQ_TASKS);
         s.tile_b = o;
         o = align16(o + 4 * (size_t)T * M * K);
+        s.tile_p2 = s.tile_b2 = s.bars = o;
+        if (nbuf == 2) {
+            s.tile_p2 = o;
+            o = align16(o + 4 * (size_t)T * M);
+            s.tile_b2 = o;
+            o = align16(o + 4 * (size_t)T * M * K);
+            s.bars = o;
+            o = align16(o + 16);
+        }
     }
     s.total = o;
     return s;
@@ -165,12 +177,16 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
 #pragma unroll
             for (int q = 0; q < 6; ++q) r6.zero(q * K + k);
         } else {
-            float t = 0.f;
+            float t = 0.f, dl = 0.f;
             if (MODE == MODE_REFINE) {
                 const SelK sk = S.sel[k];
-                t = sk.state == 1 ? low_bound(__uint_as_float(sk.lo), lf) : __int_as_float(0x7f800000);
+                // a bucketed step reads every positive breakpoint
+                t = sk.state == 1   ? low_bound(__uint_as_float(sk.lo), lf)
+                    : sk.state == 2 ? low_bound(__uint_as_float(1u), lf)
+                                    : __int_as_float(0x7f800000);
+                dl = sk.bdelta;
             }
-            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, 0.f, 0.f, t);
+            ((float4 *)(smem + L.kinfo))[k] = make_float4(lf, dl, 0.f, t);
         }
         if (MODE == MODE_REFINE) {
             SelK sk = S.sel[k];
@@ -180,6 +196,10 @@ __device__ __forceinline__ void init_block_state(const Params &P, const Scratch 
                 uint32_t width = sk.hi - sk.lo;
                 int sh = bitlen(width - 1) - 8;
                 shift[k] = sh > 0 ? sh : 0;
+            } else if (sk.state == 2) {  // bucketed step: every positive key
+                lo[k] = 1u;
+                hi[k] = KEY_INF;
+                shift[k] = -1;
             } else {
                 lo[k] = 0;
                 hi[k] = 0;
@@ -260,6 +280,7 @@ __device__ __forceinline__ RefineSink make_refine_sink(const Params &P, const Sc
     rs.lo = (const uint32_t *)(smem + L.lo);
     rs.hi = (const uint32_t *)(smem + L.hi);
     rs.shift = (const int32_t *)(smem + L.shift);
+    rs.kinfo = (const float4 *)(smem + L.kinfo);
     rs.subhist = S.subhist;
     rs.bcnt = (uint32_t *)(smem + L.bcnt);
     rs.buf = S.buf;
@@ -1149,21 +1170,26 @@ __global__ void __launch_bounds__(RARE_THREADS, 2) rare_kernel(Params P, Scratch
 // One tile of nu users starting at u0 (T users per tile): stage, reduce,
 // Algorithm 1, then consumption and Algorithm 4's Map per (user, knapsack).
 template <int MAXM, int MODE, int THREADS>
+// staged: the tile's p and b are already in shared memory at tp_s / tb_s
+// (the double-buffered pass; the caller synchronised the block after them);
+// otherwise they are loaded here into the layout's single stage buffers.
 __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, const SmemLayout &L,
                                            unsigned char *smem, int64_t u0, int nu, int T,
                                            uint32_t *x_bits, unsigned long long &dsum,
-                                           unsigned long long &psum) {
+                                           unsigned long long &psum, float *tp_s = nullptr,
+                                           float *tb_s = nullptr) {
     const int M = P.M, K = P.K;
     const float *lamf = (const float *)(smem + L.lamf);
     const SFix rfix{(uint32_t *)(smem + L.rfix), K};
-    float *tp = (float *)(smem + L.tile_p);
-    float *tb = (float *)(smem + L.tile_b);
+    const bool staged = tb_s != nullptr;
+    float *tp = staged ? tp_s : (float *)(smem + L.tile_p);
+    float *tb = staged ? tb_s : (float *)(smem + L.tile_b);
     float *pt = (float *)(smem + L.rows);
     uint64_t *selm = (uint64_t *)(smem + L.selm);
     const bool b_al = ((reinterpret_cast<uintptr_t>(P.b) & 15u) == 0) && ((M * K) % 4 == 0 || T % 4 == 0);
     const bool p_al = ((reinterpret_cast<uintptr_t>(P.p) & 15u) == 0) && ((M % 4) == 0 || T % 4 == 0);
     // stage the tile
-    {
+    if (!staged) {
         const size_t nb = (size_t)nu * M * K;
         const float *src = P.b + (size_t)u0 * M * K;
         if (b_al) {
@@ -1187,7 +1213,7 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
             for (size_t q = threadIdx.x; q < npn; q += THREADS) tp[q] = __ldg(ps + q);
         }
     }
-    __syncthreads();
+    if (!staged) __syncthreads();
     // Sec. 4.2 reduced costs, four partial sums per item
     for (int idx = threadIdx.x; idx < nu * M; idx += THREADS) {
         const float *br = tb + (size_t)idx * K;
@@ -1401,21 +1427,108 @@ __device__ __forceinline__ void dense_tile(const Params &P, const Scratch &S, co
     __syncthreads();
 }
 
+// Longest wait for a tile's bulk copies (ns): far above any copy's duration;
+// reaching it sets KP_ETIMEOUT in the device status.
+constexpr uint64_t STAGE_WAIT_NS = 2000000000ull;
+
+// pipe = 1: the tiles are staged by bulk asynchronous copies into two
+// buffers, the next tile's copy issued (by one thread) before the current
+// tile is computed, completion counted on one mbarrier per buffer; needs p and
+// b 16-byte aligned and T a multiple of 4 (every tile then starts on a 16-byte
+// boundary; the bytes of a ragged last tile beyond a multiple of 16 are loaded
+// directly).  pipe = 0: each tile is loaded synchronously, then computed.
 template <int MAXM, int MODE, int THREADS>
 __global__ void __launch_bounds__(THREADS, 2) dense_pass_kernel(Params P, Scratch S, const double *lam,
-                                                             uint32_t *x_bits, int round, int T) {
+                                                             uint32_t *x_bits, int round, int T, int pipe) {
     extern __shared__ __align__(16) unsigned char smem[];
     if (MODE == MODE_REFINE && S.ctr->n_unres[round] == 0) return;
     if (MODE != MODE_STATE && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&S.ctr->stats[0], 1ull);
-    const SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, THREADS, T, MODE);
+    const SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, THREADS, T, MODE, 1, pipe ? 2 : 1);
     init_block_state<MODE>(P, S, lam, L, smem, round, blockIdx.x == 0);
     __syncthreads();
     unsigned long long dsum = 0ull, psum = 0ull;
     const int64_t ntiles = (P.N + T - 1) / T;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (!pipe) {
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int64_t u0 = tile * T;
+            const int nu = (int)((P.N - u0) < T ? (P.N - u0) : T);
+            dense_tile<MAXM, MODE, THREADS>(P, S, L, smem, u0, nu, T, x_bits, dsum, psum);
+        }
+        flush_block_state<MODE>(P, S, L, smem, dsum, psum);
+        return;
+    }
+    const int M = P.M, K = P.K;
+    uint64_t *bar = (uint64_t *)(smem + L.bars);
+    float *tpb[2] = {(float *)(smem + L.tile_p), (float *)(smem + L.tile_p2)};
+    float *tbb[2] = {(float *)(smem + L.tile_b), (float *)(smem + L.tile_b2)};
+    // bytes of a tile the bulk copies take (multiples of 16) and all its bytes
+    auto tile_users = [&](int64_t tile) {
         const int64_t u0 = tile * T;
-        const int nu = (int)((P.N - u0) < T ? (P.N - u0) : T);
-        dense_tile<MAXM, MODE, THREADS>(P, S, L, smem, u0, nu, T, x_bits, dsum, psum);
+        return (int)((P.N - u0) < T ? (P.N - u0) : T);
+    };
+    auto issue = [&](int64_t tile, int buf) {  // one thread
+        const int64_t u0 = tile * T;
+        const int nu = tile_users(tile);
+        const uint32_t bb = (uint32_t)(((size_t)nu * M * K * 4) & ~(size_t)15);
+        const uint32_t bp = (uint32_t)(((size_t)nu * M * 4) & ~(size_t)15);
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(&bar[buf], bb + bp);
+        if (bb) bulk_copy_g2s(tbb[buf], P.b + (size_t)u0 * M * K, bb, &bar[buf]);
+        if (bp) bulk_copy_g2s(tpb[buf], P.p + (size_t)u0 * M, bp, &bar[buf]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // thread 0's count, per buffer, of the copies issued and of the phases it saw complete
+    uint32_t iss0 = 0u, iss1 = 0u, done0 = 0u, done1 = 0u;
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles && threadIdx.x == 0) {
+        issue(tile, 0);
+        ++iss0;
+    }
+    bool ok = true;
+    for (int n = 0; tile < ntiles; tile += gridDim.x, ++n) {
+        const int cur = n & 1;
+        const int64_t nxt = tile + gridDim.x;
+        // the other buffer was last read by the previous tile, which every
+        // thread finished (the barrier at the end of dense_tile)
+        if (nxt < ntiles && threadIdx.x == 0) {
+            issue(nxt, cur ^ 1);
+            if (cur) ++iss0;
+            else ++iss1;
+        }
+        const bool got = mbar_wait(&bar[cur], (uint32_t)((n >> 1) & 1), STAGE_WAIT_NS);
+        if (threadIdx.x == 0 && got) {
+            if (cur) ++done1;
+            else ++done0;
+        }
+        ok = __syncthreads_and(got) != 0;
+        if (!ok) break;
+        const int64_t u0 = tile * T;
+        const int nu = tile_users(tile);
+        {  // the bytes past the last multiple of 16 (ragged last tile)
+            const size_t nb = (size_t)nu * M * K, np = (size_t)nu * M;
+            for (size_t q = ((nb * 4) & ~(size_t)15) / 4 + threadIdx.x; q < nb; q += THREADS)
+                tbb[cur][q] = __ldg(P.b + (size_t)u0 * M * K + q);
+            for (size_t q = ((np * 4) & ~(size_t)15) / 4 + threadIdx.x; q < np; q += THREADS)
+                tpb[cur][q] = __ldg(P.p + (size_t)u0 * M + q);
+        }
+        __syncthreads();
+        dense_tile<MAXM, MODE, THREADS>(P, S, L, smem, u0, nu, T, x_bits, dsum, psum, tpb[cur], tbb[cur]);
+    }
+    if (!ok) {
+        // a copy did not complete in time: report it and wait (bounded) for
+        // every copy still in flight, so that none lands after the block left
+        if (threadIdx.x == 0) {
+            atomicOr(&S.ctr->status, 1 << KP_ETIMEOUT);
+            for (uint32_t w = done0; w < iss0; ++w) (void)mbar_wait(&bar[0], w & 1u, STAGE_WAIT_NS);
+            for (uint32_t w = done1; w < iss1; ++w) (void)mbar_wait(&bar[1], w & 1u, STAGE_WAIT_NS);
+        }
+        __syncthreads();
+        return;
     }
     flush_block_state<MODE>(P, S, L, smem, dsum, psum);
 }
@@ -1520,16 +1633,29 @@ cudaError_t launch_csr(const Params &P, const Scratch &S, const double *lam, uin
 template <int MAXM, int MODE>
 cudaError_t launch_dense(const Params &P, const Scratch &S, const double *lam, uint32_t *x_bits,
                          int round, cudaStream_t st, int *occupancy_out) {
-    const int T = P.tile > 0 ? P.tile : dense_tile_users(P);
-    SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, DENSE_THREADS, T, MODE);
+    int T = P.tile > 0 ? P.tile : dense_tile_users(P);
     auto kern = dense_pass_kernel<MAXM, MODE, DENSE_THREADS>;
     static int max_dyn = -1;
     cudaError_t e = prepare_kernel(kern, &max_dyn);
     if (e != cudaSuccess) return e;
+    // staging mode 1: double-buffered with half a tile per buffer (the two
+    // buffers take the shared memory of one tile, so as many blocks fit on an
+    // SM); needs 16-byte aligned p and b and a buffer of a multiple of 4 users
+    int pipe = 0;
+    SmemLayout L = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, DENSE_THREADS, T, MODE);
+    const int Th = (T / 2) & ~3;
+    if (P.stage == 1 && Th >= 4 && (reinterpret_cast<uintptr_t>(P.b) & 15u) == 0 && (reinterpret_cast<uintptr_t>(P.p) & 15u) == 0) {
+        const SmemLayout L2 = smem_layout(KP_B_DENSE, P.K, P.M, MAXM, DENSE_THREADS, Th, MODE, 1, 2);
+        if (L2.total <= (size_t)max_dyn) {
+            pipe = 1;
+            T = Th;
+            L = L2;
+        }
+    }
     if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
     if (occupancy_out)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, DENSE_THREADS, L.total);
-    kern<<<S.G, DENSE_THREADS, L.total, st>>>(P, S, lam, x_bits, round, T);
+    kern<<<S.G, DENSE_THREADS, L.total, st>>>(P, S, lam, x_bits, round, T, pipe);
     return cudaGetLastError();
 }
 

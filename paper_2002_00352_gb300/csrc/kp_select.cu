@@ -579,6 +579,83 @@ cudaError_t launch_batch_select(const BatchDev &B, int64_t totK, const double *l
     return cudaGetLastError();
 }
 
+// Bucketed Reduce of Sec. 5.2.  Prep: every knapsack to state 2 with its
+// bucket width Delta_k = delta lambda_k^t (delta where lambda_k^t = 0), the
+// bucket masses cleared, the re-run pass of BUCKET_ROUND enabled.
+__global__ void bucket_prep_kernel(Params P, Scratch S, const double *lam, double delta) {
+    const int K = P.K;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < K * NSUB; q += gridDim.x * blockDim.x) {
+        S.subhist[q] = 0ull;
+        if (q < K) {
+            const double l = lam[q];
+            const float dl = (float)(l > 0.0 ? delta * l : delta);
+            S.sel[q].state = 2;
+            S.sel[q].bdelta = dl > FLT_MIN ? dl : FLT_MIN;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.ctr->n_unres[BUCKET_ROUND] = K;
+}
+
+// Select: walking down from the highest bucket, the first bucket whose mass
+// takes the cumulative mass above B_k holds the threshold; inside it the mass
+// is taken as uniform over the bucket's range [lo, hi) and lambda_k^{t+1} is
+// the point where the cumulative mass reaches B_k (linear interpolation),
+// clamped to the bucket and to lambda >= 0.  No bucket crosses B_k (the whole
+// emitted mass is within the budget): lambda_k^{t+1} = 0, as in Algorithm 4.
+// Integer fixed-point masses locate the bucket exactly; the interpolation is FP64.
+__global__ void bucket_select_kernel(Params P, Scratch S, const double *lam, double *lam_next) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P.K) return;
+    const unsigned long long *h = S.subhist + (size_t)k * NSUB;
+    const unsigned long long Bfix = budget_fixed(P.B[k], P.fixs);
+    unsigned long long A = 0ull;
+    int hit = -1;
+    for (int b = NSUB - 1; b >= 1; --b) {
+        const unsigned long long m = h[b];
+        if (A + m > Bfix) {
+            hit = b;
+            break;
+        }
+        A += m;
+    }
+    double out = 0.0;
+    if (hit >= 0) {
+        const double lt = (double)(float)lam[k], dl = (double)S.sel[k].bdelta;
+        const int id = hit - 128;
+        double lo, hi;
+        if (id == 0) {
+            lo = lt - dl;
+            hi = lt + dl;
+        } else if (id > 0) {
+            lo = lt + ldexp(dl, id - 1);
+            hi = lt + ldexp(dl, id);
+        } else {
+            lo = lt - ldexp(dl, -id);
+            hi = lt - ldexp(dl, -id - 1);
+        }
+        const double f = (double)(Bfix - A) / (double)h[hit];
+        out = hi - f * (hi - lo);
+        out = fmin(fmax(out, lo), hi);
+        out = fmax(out, 0.0);
+    }
+    lam_next[k] = out;
+    S.sel[k].state = 0;
+    if (k == 0) S.ctr->n_unres[BUCKET_ROUND] = 0;
+}
+
+cudaError_t launch_bucket_prep(const Params &P, const Scratch &S, const double *lambda, double delta,
+                               cudaStream_t st) {
+    const int n = P.K * NSUB;
+    bucket_prep_kernel<<<(n + 255) / 256, 256, 0, st>>>(P, S, lambda, delta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_select(const Params &P, const Scratch &S, const double *lambda, double *lambda_next,
+                                 cudaStream_t st) {
+    bucket_select_kernel<<<(P.K + 127) / 128, 128, 0, st>>>(P, S, lambda, lambda_next);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_select(const Params &P, const Scratch &S, const double *lambda,
                           double *lambda_next, int round, cudaStream_t st) {
     select_kernel<<<P.K, 256, 0, st>>>(P, S, lambda, lambda_next, round);

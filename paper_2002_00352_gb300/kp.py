@@ -58,7 +58,7 @@ EXPORTS = [
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
     "kp_autotune", "kp_limits", "kp_bcd_step", "kp_shard_group_create", "kp_shard_group_destroy",
-    "kp_shard_group_scd_step",
+    "kp_shard_group_scd_step", "kp_scd_step_bucketed", "kp_set_tile",
 ]
 
 
@@ -95,6 +95,8 @@ def load_library(path: Optional[str] = None):
     lib.kp_autotune.argtypes = [P, ctypes.POINTER(ctypes.c_int32), P]
     lib.kp_limits.argtypes = [ctypes.POINTER(ctypes.c_int32)]
     lib.kp_bcd_step.argtypes = [P, P, P, P, P, P, P]
+    lib.kp_scd_step_bucketed.argtypes = [P, P, f64, P, P]
+    lib.kp_set_tile.argtypes = [P, i32, i32]
     lib.kp_shard_group_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32, ctypes.POINTER(ctypes.c_void_p)]
     lib.kp_shard_group_destroy.argtypes = [P]
     lib.kp_shard_group_scd_step.argtypes = [P, P, P, P, P, P, P]
@@ -286,6 +288,19 @@ def kp_bcd_step(prob: Problem, lam, block, lam_next, dual_sum=None, primal_sum=N
                                       _ptr(lam_next, torch.float64, "lambda_next"),
                                       _ptr(dual_sum, torch.float64, "dual_sum"),
                                       _ptr(primal_sum, torch.float64, "primal_sum"), _stream(stream)))
+
+
+def kp_scd_step_bucketed(prob: Problem, lam, delta: float, lam_next, stream=None):
+    """Algorithm 4 with the bucketed, interpolated Reduce of Sec. 5.2 (bucket
+    width delta * lambda_k, or delta where lambda_k = 0)."""
+    _check(load_library().kp_scd_step_bucketed(prob.handle, _ptr(lam, torch.float64, "lambda"), float(delta),
+                                               _ptr(lam_next, torch.float64, "lambda_next"), _stream(stream)))
+
+
+def kp_set_tile(prob: Problem, users: int, staging: int):
+    """Dense instances: users per shared-memory tile and staging mode (0 loads by the
+    threads, 1 double-buffered bulk asynchronous copies)."""
+    _check(load_library().kp_set_tile(prob.handle, int(users), int(staging)))
 
 
 def kp_dual_backward(prob: Problem, lam, x_bits, R, upstream, grad_lambda=None, grad_p=None,

@@ -487,6 +487,43 @@ def test_graph_replay_matches_eager():
     assert torch.equal(g.lam, eager)
 
 
+@pytest.mark.parametrize("case", ["hier_m20", "dense_2e7", "ragged"])
+def test_staging_modes_agree(case):
+    """The dense passes give the same bits whether each tile is loaded by the
+    block's threads (staging 0) or double-buffered by bulk asynchronous copies
+    (staging 1), at several tile sizes: four SCD steps from lambda = 0 (breakpoint
+    and re-run passes), then the consumption pass.  The ragged case has a last
+    tile whose b and p rows end off a 16-byte boundary (60 bytes of b and 20 of p
+    per user), loaded past the bulk copy's end."""
+    if case == "hier_m20":
+        inst = gen.hier_m20(N=30_000, device="cuda")
+    elif case == "dense_2e7":
+        inst = gen.dense_2e7(N=20_000, device="cuda")
+    else:
+        inst = gen.random_small(2001, 5, 3, seed=9, device="cuda", layout="dense", frac=0.2)
+    runs = []
+    for staging, tile in ((0, 0), (1, 0), (1, 12), (1, 8)):
+        prob = _problem(inst)
+        kp.kp_set_tile(prob, tile, staging)
+        lam = torch.zeros(inst.K, dtype=torch.float64, device="cuda")
+        nxt, R = torch.zeros_like(lam), torch.zeros_like(lam)
+        d, pr = torch.zeros(1, dtype=torch.float64, device="cuda"), torch.zeros(1, dtype=torch.float64, device="cuda")
+        out = []
+        for _ in range(4):
+            kp.kp_scd_step(prob, lam, nxt, R=R, dual_sum=d, primal_sum=pr)
+            out += [nxt.clone(), R.clone(), d.clone(), pr.clone()]
+            lam, nxt = nxt, lam
+        kp.kp_reduce_consumption(prob, lam, R=R, dual_sum=d, primal_sum=pr)
+        out += [R.clone(), d.clone(), pr.clone()]
+        kp.kp_device_status(prob)
+        runs.append(out)
+    for r in runs[1:]:
+        for a_, b_ in zip(runs[0], r):
+            assert torch.equal(a_, b_)
+    with pytest.raises(kp.KpError):
+        kp.kp_set_tile(prob, 0, 2)
+
+
 def test_autotune_keeps_results():
     inst = gen.hier_m20(N=30_000, device="cuda")
     prob = _problem(inst)

@@ -660,3 +660,80 @@ def test_categorical_expansion_is_the_integer_optimum(seed):
         xi = fold_decisions(torch.tensor(x2)[None], u)[0].numpy()
         assert all(0 <= xi[j] <= u[j] for j in range(M))
         assert float(pt @ xi) == pytest.approx(best, abs=1e-12)
+
+
+def test_bucket_ids_at_the_boundaries():
+    """Sec. 5.2 buckets (id 0 for |d| < Delta, else sign(d) (1 + floor(log2(|d| / Delta)))),
+    with lambda_k^t = 1 and Delta = 0.25, both exact in FP32: a boundary value belongs
+    to the bucket above it in |d|, ids are clamped at 127."""
+    v = np.array([1.0, 1.2499, 1.25, 1.4999, 1.5, 2.0, 2.0001, 0.7501, 0.75, 0.5, 0.4999,
+                  1.0 + 2.0 ** 100, 2.0 ** 125, 2.0 ** 126])
+    # 2^100 / 0.25 = 2^102: 1 + 102; 2^125 / 0.25 = 2^127: 128, clamped; 2^126 / 0.25
+    # overflows FP32 to inf: clamped
+    want = [0, 0, 1, 1, 2, 3, 3, 0, -1, -2, -2, 103, 127, 127]
+    assert oracle.bucket_ids(v, 1.0, 0.25).tolist() == want
+
+
+def test_bucket_reduce_worked_example():
+    """Hand-worked example of the bucketed Reduce: lambda^t = 1, Delta = 0.1 (FP32:
+    0.100000001490116), candidates 1.05 (mass 1, bucket 0 = [0.9, 1.1)), 1.15 (mass
+    2, bucket 1 = [1.1, 1.2)), 1.35 (mass 4, bucket 2 = [1.2, 1.4)), 0.7 (mass 8,
+    bucket -2 = [0.6, 0.8)).
+      B = 4.5: bucket 2 leaves 4 <= 4.5, bucket 1 takes it to 6: 1.2 - (0.5 / 2) 0.1
+      B = 5:   1.2 - (1 / 2) 0.1 = 1.15
+      B = 0.5: bucket 2 crosses: 1.4 - (0.5 / 4) 0.2 = 1.375
+      B = 14:  7 above bucket -2, which crosses: 0.8 - (7 / 8) 0.2 = 0.625
+      B = 15:  the whole mass fits: 0."""
+    v1 = np.array([1.05, 1.15, 1.35, 0.7])
+    v2 = np.array([1.0, 2.0, 4.0, 8.0])
+    d = float(np.float32(0.1))
+    for Bk, want in [(4.5, 1.0 + 2 * d - 0.25 * d), (5.0, 1.0 + 2 * d - 0.5 * d), (0.5, 1.0 + 4 * d - 0.125 * 2 * d),
+                     (14.0, 1.0 - 2 * d - 0.875 * 2 * d), (15.0, 0.0)]:
+        got = oracle.bucket_reduce(v1, v2, Bk, 1.0, oracle.bucket_delta(1.0, 0.1))
+        assert got == pytest.approx(want, abs=1e-12), (Bk, got, want)
+    # the worked numbers themselves
+    assert oracle.bucket_reduce(v1, v2, 4.5, 1.0, oracle.bucket_delta(1.0, 0.1)) == pytest.approx(1.175, abs=1e-8)
+    assert oracle.bucket_reduce(v1, v2, 14.0, 1.0, oracle.bucket_delta(1.0, 0.1)) == pytest.approx(0.625, abs=1e-8)
+
+
+def test_bucket_reduce_one_bucket_closed_form():
+    """With every candidate inside bucket 0 the mass is spread uniformly over
+    [lambda^t - Delta, lambda^t + Delta): the threshold is lambda^t + Delta - 2 Delta B / M
+    (M the total mass), or 0 when B >= M."""
+    rng = np.random.default_rng(11)
+    lt, dl = 2.0, np.float32(0.5)
+    v1 = rng.uniform(1.6, 2.4, size=50)
+    v2 = rng.uniform(0.1, 1.0, size=50)
+    Mt = v2.sum()
+    for frac in (0.1, 0.5, 0.9):
+        got = oracle.bucket_reduce(v1, v2, frac * Mt, lt, dl)
+        assert got == pytest.approx(lt + float(dl) - 2 * float(dl) * frac, rel=1e-12)
+    assert oracle.bucket_reduce(v1, v2, Mt * 1.0001, lt, dl) == 0.0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_bucketed_reduce_brackets_the_exact_reduce(seed):
+    """The exact threshold of Algorithm 4 (pinned above by its definition) lies in
+    the bucket the bucketed Reduce interpolates in, so the two differ by at most that
+    bucket's width; the buckets are monotone in v, so the crossing bucket is the
+    exact threshold's."""
+    rng = np.random.default_rng(1400 + seed)
+    N, M, K = 60, 6, 3
+    S, C = random_laminar(M, rng)
+    p = rng.uniform(0, 1, size=(N, M))
+    b = rng.uniform(0, 1, size=(N, M, K))
+    B = 0.15 * b.sum(axis=(0, 1))
+    lam = rng.uniform(0.2, 0.8, size=K)
+    exact, _, _ = oracle.scd_step(p, b, S, C, lam, B)
+    _, ek, v1, v2 = oracle.scd_map_users(p, b, S, C, lam)
+    for delta in (1e-4, 1e-2, 0.5):
+        for k in range(K):
+            sel = ek == k
+            dk = oracle.bucket_delta(lam[k], delta)
+            got = oracle.bucket_reduce(v1[sel], v2[sel], B[k], lam[k], dk)
+            if exact[k] == 0.0:
+                assert got == 0.0 or v2[sel][v1[sel] > 0].sum() > B[k]
+                continue
+            idb = int(oracle.bucket_ids(np.array([exact[k]]), lam[k], dk)[0])
+            lo, hi = oracle.bucket_range(idb, lam[k], dk)
+            assert abs(got - exact[k]) <= (hi - lo) * (1 + 1e-9), (seed, delta, k, got, exact[k], lo, hi)
