@@ -307,8 +307,8 @@ kp_status kp_reduce_consumption_noalloc(const kp_desc *desc, const double *lambd
 kp_status kp_autotune(kp_problem *h, int32_t *chosen, void *stream);
 
 /* Dense instances: the users per shared-memory tile (1 .. the default, which
- * fills a 64 KB tile of b; 0 = the default) and the staging mode of the user
- * passes:
+ * fills a 64 KB tile of b and at most 96 KB of everything staged per user;
+ * 0 = the default) and the staging mode of the user passes:
  * 0 = each tile loaded by the block's threads, then computed (two blocks per
  * SM overlap one's loads with the other's work); 1 = two buffers of half a
  * tile each, the next tile's p and b brought in by 1-D bulk asynchronous

@@ -32,6 +32,7 @@ namespace kp {
 namespace {
 
 constexpr int DENSE_TILE_BYTES = 64 * 1024;   // dense b tile
+constexpr int DENSE_USER_BYTES = 96 * 1024;   // all per-user staging of a dense tile
 
 struct SmemLayout {
     size_t lamf, kinfo, bcnt, lo, hi, shift, rfix, reg3, rows, tile_p, tile_b, selm, red, dq;
@@ -1592,6 +1593,11 @@ int max_optin_smem() {
 }
 
 constexpr int CSR_THREADS = 512;
+// the consumption pass (no breakpoints) of rows of up to 10 items needs fewer
+// registers: 24 warps per SM instead of 16 hide more of its load latency
+constexpr int CSR_STATE_THREADS = 768;
+template <int MAXM, int MODE>
+constexpr int csr_threads() { return MODE == MODE_STATE && MAXM <= 10 ? CSR_STATE_THREADS : CSR_THREADS; }
 constexpr int DENSE_THREADS = 256;
 
 
@@ -1611,22 +1617,23 @@ cudaError_t prepare_kernel(Kern kern, int *max_dyn) {
 template <int MAXM, int C, int MODE>
 cudaError_t launch_csr(const Params &P, const Scratch &S, const double *lam, uint32_t *x_bits,
                        int round, cudaStream_t st, int *occupancy_out) {
-    auto kern = csr_pass_kernel<MAXM, C, MODE, CSR_THREADS>;
+    constexpr int THR = csr_threads<MAXM, MODE>();
+    auto kern = csr_pass_kernel<MAXM, C, MODE, THR>;
     static int max_dyn = -1;  // once per instantiation, before any stream capture
     cudaError_t e = prepare_kernel(kern, &max_dyn);
     if (e != cudaSuccess) return e;
     // regular rows: per-warp pair queues (sets = 0) when they fit next to the
     // per-knapsack state, else per-thread rows swept after every tile
     int sets = (C > 0 && MODE != MODE_STATE && MAXM <= 16) ? 0 : 1;
-    SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE, sets);
+    SmemLayout L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, THR, 0, MODE, sets);
     if (L.total > (size_t)max_dyn && sets != 1) {
         sets = 1;
-        L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, CSR_THREADS, 0, MODE, sets);
+        L = smem_layout(KP_B_CSR, P.K, P.M, MAXM, THR, 0, MODE, sets);
     }
     if (L.total > (size_t)max_dyn) return cudaErrorInvalidConfiguration;
     if (occupancy_out)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, CSR_THREADS, L.total);
-    kern<<<S.G, CSR_THREADS, L.total, st>>>(P, S, lam, x_bits, round, sets);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occupancy_out, kern, THR, L.total);
+    kern<<<S.G, THR, L.total, st>>>(P, S, lam, x_bits, round, sets);
     return cudaGetLastError();
 }
 
@@ -1722,10 +1729,14 @@ cudaError_t batch_dispatch(const BatchDev &B, int maxm, size_t smem, int grid, c
 
 }  // namespace
 
-// Users per shared-memory tile of the dense pass (a 64 KB tile of b).
+// Users per shared-memory tile of the dense pass: a 64 KB tile of b, and at
+// most 96 KB for everything staged per user (b, p, p~ and the selection), so
+// that two blocks fit on an SM also when K is small and M large.
 int dense_tile_users(const Params &P) {
     long long per = (long long)P.M * P.K * 4;
     long long T = DENSE_TILE_BYTES / per;
+    const long long T2 = DENSE_USER_BYTES / (per + 8LL * P.M + 8);
+    if (T2 < T) T = T2;
     if (T > 256) T = 256;
     if (T >= 4) T &= ~3LL;
     if (T < 1) T = 1;
@@ -1823,7 +1834,10 @@ int pass_grid_size(const Params &P) {
 
 size_t pass_smem_bytes(const Params &P, int mode) {
     int maxm = P.M <= 8 ? 8 : (P.M <= 10 ? 10 : (P.M <= 16 ? 16 : 64));
-    if (P.layout == KP_B_CSR) return smem_layout(KP_B_CSR, P.K, P.M, maxm, CSR_THREADS, 0, mode).total;
+    if (P.layout == KP_B_CSR)
+        return smem_layout(KP_B_CSR, P.K, P.M, maxm, mode == MODE_STATE && maxm <= 10 ? CSR_STATE_THREADS : CSR_THREADS,
+                           0, mode)
+            .total;
     return smem_layout(KP_B_DENSE, P.K, P.M, maxm, DENSE_THREADS, dense_tile_users(P), mode).total;
 }
 
