@@ -319,6 +319,14 @@ kp_status kp_autotune(kp_problem *h, int32_t *chosen, void *stream);
  * a CSR instance or values out of range.  (Not in the paper.) */
 kp_status kp_set_tile(kp_problem *h, int32_t users, int32_t staging);
 
+/* Exercises the bounded wait of staging mode 1 without a fault: one block
+ * waits on an mbarrier that nothing arrives on, gives up after limit_ns
+ * nanoseconds (1e3 .. 1e9) and reports KP_ETIMEOUT through its status word,
+ * leaving the context usable.  Returns KP_ETIMEOUT (the expected outcome),
+ * KP_OK if the wait completed (it cannot), KP_EINVAL for a limit out of
+ * range.  Synchronous; allocates 4 bytes for the call. */
+kp_status kp_wait_selftest(int64_t limit_ns, void *stream);
+
 /* Synchronises the stream and returns the device-side status accumulated by
  * the handle's kernels since the last call (KP_OK, KP_ETIMEOUT or
  * KP_ESTATE), then clears it.  KP_ETIMEOUT: a dense user pass waited more

@@ -547,6 +547,22 @@ kp_status kp_info(kp_problem *h, int64_t out[4]) {
     return KP_OK;
 }
 
+kp_status kp_wait_selftest(int64_t limit_ns, void *stream) {
+    if (limit_ns < 1000 || limit_ns > 1000000000) return fail(KP_EINVAL, "kp_wait_selftest: limit_ns must be in [1e3, 1e9]");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *d = nullptr;
+    KP_CUDA(cudaMalloc(&d, sizeof(int32_t)), "cudaMalloc");
+    int32_t status = 0;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = kp::launch_wait_selftest((uint64_t)limit_ns, d, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "kp_wait_selftest");
+    if (status & (1 << KP_ETIMEOUT)) return fail(KP_ETIMEOUT, "kp_wait_selftest: the wait ran out (expected)");
+    return KP_OK;
+}
+
 kp_status kp_limits(int32_t out[3]) {
     if (!out) return fail(KP_EINVAL, "kp_limits: NULL argument");
     out[0] = KP_MAX_M;

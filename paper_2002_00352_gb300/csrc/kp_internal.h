@@ -184,6 +184,7 @@ cudaError_t launch_backward(const Params &P, const double *lambda, const uint32_
                             const double *R, const double *upstream, double *grad_lambda,
                             float *grad_p, double *grad_B, cudaStream_t st);
 cudaError_t launch_validate(const Params &P, uint32_t *flags, cudaStream_t st);
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int32_t *status, cudaStream_t st);
 cudaError_t launch_shmask(const Params &P, uint2 *shmask, unsigned long long *rare, int64_t cap,
                           unsigned long long *count, cudaStream_t st);
 // kp_api.cu

@@ -1841,4 +1841,26 @@ size_t pass_smem_bytes(const Params &P, int mode) {
     return smem_layout(KP_B_DENSE, P.K, P.M, maxm, DENSE_THREADS, dense_tile_users(P), mode).total;
 }
 
+namespace {
+
+// One mbarrier that nothing arrives on: the staging pass's bounded wait runs
+// out after limit_ns and the kernel reports it as the passes do.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int32_t *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const bool got = mbar_wait(&bar, 0u, limit_ns);
+    if (threadIdx.x == 0 && !got) atomicOr(status, 1 << KP_ETIMEOUT);
+}
+
+}  // namespace
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int32_t *status, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, status);
+    return cudaGetLastError();
+}
+
 }  // namespace kp

@@ -58,7 +58,7 @@ EXPORTS = [
     "kp_reduce_consumption_noalloc", "kp_batch_create", "kp_batch_destroy", "kp_batch_layout",
     "kp_batch_reduce_consumption", "kp_batch_dd_step", "kp_batch_scd_step", "kp_batch_device_status",
     "kp_autotune", "kp_limits", "kp_bcd_step", "kp_shard_group_create", "kp_shard_group_destroy",
-    "kp_shard_group_scd_step", "kp_scd_step_bucketed", "kp_set_tile",
+    "kp_shard_group_scd_step", "kp_scd_step_bucketed", "kp_set_tile", "kp_wait_selftest",
 ]
 
 
@@ -97,6 +97,7 @@ def load_library(path: Optional[str] = None):
     lib.kp_bcd_step.argtypes = [P, P, P, P, P, P, P]
     lib.kp_scd_step_bucketed.argtypes = [P, P, f64, P, P]
     lib.kp_set_tile.argtypes = [P, i32, i32]
+    lib.kp_wait_selftest.argtypes = [i64, P]
     lib.kp_shard_group_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32, ctypes.POINTER(ctypes.c_void_p)]
     lib.kp_shard_group_destroy.argtypes = [P]
     lib.kp_shard_group_scd_step.argtypes = [P, P, P, P, P, P, P]
@@ -301,6 +302,11 @@ def kp_set_tile(prob: Problem, users: int, staging: int):
     """Dense instances: users per shared-memory tile and staging mode (0 loads by the
     threads, 1 double-buffered bulk asynchronous copies)."""
     _check(load_library().kp_set_tile(prob.handle, int(users), int(staging)))
+
+
+def kp_wait_selftest(limit_ns: int, stream=None):
+    """Runs the bounded-wait self-test; raises KpError with status KP_ETIMEOUT (expected)."""
+    _check(load_library().kp_wait_selftest(int(limit_ns), _stream(stream)))
 
 
 def kp_dual_backward(prob: Problem, lam, x_bits, R, upstream, grad_lambda=None, grad_p=None,

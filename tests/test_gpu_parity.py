@@ -524,6 +524,27 @@ def test_staging_modes_agree(case):
         kp.kp_set_tile(prob, 0, 2)
 
 
+def test_bounded_wait_reports_timeout():
+    """Failure detection without a fault: a wait on an mbarrier that nothing arrives
+    on (the wait of staging mode 1) gives up after its limit and reports KP_ETIMEOUT
+    through the status word; the context stays usable (a step runs after it)."""
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(kp.KpError) as ei:
+        kp.kp_wait_selftest(2_000_000)
+    assert ei.value.status == kp.KP_ETIMEOUT
+    assert time.perf_counter() - t0 >= 2e-3
+    with pytest.raises(kp.KpError) as ei:
+        kp.kp_wait_selftest(10)
+    assert ei.value.status == kp.KP_EINVAL
+    inst = gen.small_dd_scd(N=500, seed=3, device="cuda")
+    prob = _problem(inst)
+    lam = torch.zeros(inst.K, dtype=torch.float64, device="cuda")
+    nxt = torch.zeros_like(lam)
+    kp.kp_scd_step(prob, lam, nxt)
+    kp.kp_device_status(prob)
+
+
 def test_autotune_keeps_results():
     inst = gen.hier_m20(N=30_000, device="cuda")
     prob = _problem(inst)
