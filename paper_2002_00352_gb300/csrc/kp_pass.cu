@@ -1547,15 +1547,20 @@ __global__ void __launch_bounds__(THREADS, 2) dense_batch_kernel(BatchDev B, con
     __shared__ Params sP;
     __shared__ Scratch sS;
     __shared__ int s_skip;
-    __shared__ long long s_t;
+    __shared__ long long s_t[2];  // alternate slots: a thread still reading one never sees it rewritten
     int cur = -1;
     unsigned long long dsum = 0ull, psum = 0ull;
     SmemLayout L;
-    for (;;) {
-        if (threadIdx.x == 0) s_t = (long long)atomicAdd(&B.next[round], 1ull);
+    // thread 0 claims the next tile while the block works on the current one,
+    // so the counter's round trip is off the block's path
+    long long nxt = 0;
+    if (threadIdx.x == 0) nxt = (long long)atomicAdd(&B.next[round], 1ull);
+    for (int it = 0;; ++it) {
+        if (threadIdx.x == 0) s_t[it & 1] = nxt;
         __syncthreads();
-        const int64_t t = s_t;
+        const int64_t t = s_t[it & 1];
         if (t >= B.ntiles) break;
+        if (threadIdx.x == 0) nxt = (long long)atomicAdd(&B.next[round], 1ull);
         const int inst = B.tile_inst[t];
         if (inst != cur) {
             if (cur >= 0 && !s_skip) flush_block_state<MODE>(sP, sS, L, smem, dsum, psum);
