@@ -2,7 +2,11 @@
 // every pass over the users of all instances is one persistent launch over a
 // work list of (instance, tile of users); the selection kernels run one block
 // per (instance, knapsack).  Each instance keeps its own parameters, scratch,
-// multipliers and counters; only the launches are shared.
+// multipliers and counters; only the launches are shared.  An instance with
+// enough tiles to fill the GPU several times over ("solo") gains nothing from
+// sharing a launch: it runs its own passes, finalize and selection (the
+// kernels of a single handle) inside the batched step, and the shared launches
+// skip it.
 #include <algorithm>
 #include <cstddef>
 #include <cstdio>
@@ -24,8 +28,14 @@ struct kp_batch {
     size_t bufcnt_words = 0;
     unsigned long long *next = nullptr;
     std::vector<void *> allocs;
-    std::vector<int64_t> koff;
+    std::vector<int64_t> koff, xoff;
+    std::vector<int> solo;  // instances that run their own launches
 };
+
+namespace {
+// an instance with at least this many tiles per resident block runs solo
+constexpr int SOLO_TILES_PER_BLOCK = 4;
+}
 
 namespace {
 
@@ -118,7 +128,18 @@ kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out) {
         b->smem[m] = 0;
         for (int i = 0; i < count; ++i) b->smem[m] = std::max(b->smem[m], kp::dense_smem_bytes(b->probs[i]->P, m));
     }
-    // work list: the tiles of every instance, most expensive instances first
+    // instances that fill the GPU on their own run solo; the work list holds
+    // the tiles of every other instance, most expensive instances first
+    std::vector<uint8_t> solo(count, 0);
+    for (int i = 0; i < count; ++i) {
+        const kp::Params &P = b->probs[i]->P;
+        const int64_t tiles = (P.N + P.tile - 1) / P.tile;
+        if (tiles >= (int64_t)SOLO_TILES_PER_BLOCK * b->G) {
+            solo[i] = 1;
+            b->solo.push_back(i);
+            (void)kp::pass_grid_size(P);  // sets its kernels' attributes now, before any stream capture
+        }
+    }
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
@@ -135,6 +156,7 @@ kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out) {
         xo += P.N * P.W;
     }
     for (int i : order) {
+        if (solo[i]) continue;
         const kp::Params &P = b->probs[i]->P;
         for (int64_t u0 = 0; u0 < P.N; u0 += P.tile) {
             tile_inst.push_back(i);
@@ -194,12 +216,14 @@ kp_status kp_batch_create(const kp_desc *descs, int32_t count, kp_batch **out) {
     if (st == KP_OK) st = bcopy(b, const_cast<int64_t **>(&b->B.koff), b->koff, "batch offsets");
     if (st == KP_OK) st = bcopy(b, const_cast<int64_t **>(&b->B.xoff), xoff, "batch x offsets");
     if (st == KP_OK) st = bcopy(b, const_cast<int32_t **>(&b->B.kinst), kinst, "batch knapsack table");
+    if (st == KP_OK) st = bcopy(b, const_cast<uint8_t **>(&b->B.solo), solo, "batch solo flags");
     if (st == KP_OK) st = bcopy(b, const_cast<int32_t **>(&b->B.tile_inst), tile_inst, "batch tiles");
     if (st == KP_OK) st = bcopy(b, const_cast<int64_t **>(&b->B.tile_u0), tile_u0, "batch tiles");
     if (st != KP_OK) {
         destroy(b);
         return st;
     }
+    b->xoff = xoff;
     b->B.ntiles = b->ntiles;
     b->B.count = count;
     b->B.next = b->next;
@@ -229,6 +253,42 @@ static cudaError_t reset_pass(kp_batch *b, bool counters, bool counts, cudaStrea
     return e;
 }
 
+// The solo instances' share of a pass, finalize and selection: a single
+// handle's launches on each instance's slice of the multipliers.
+static cudaError_t solo_pass(kp_batch *b, const double *lam, int mode, int round, uint32_t *x_bits,
+                             cudaStream_t st) {
+    for (int i : b->solo) {
+        const kp_problem *h = b->probs[i];
+        cudaError_t e = kp::launch_user_pass(h->P, h->S, lam + b->koff[i], mode, round,
+                                             x_bits ? x_bits + b->xoff[i] : nullptr, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t solo_finalize(kp_batch *b, const double *lam, double *R, double *dual, double *primal,
+                                 double alpha, double *lam_next, cudaStream_t st) {
+    for (int i : b->solo) {
+        const kp_problem *h = b->probs[i];
+        const int64_t ko = b->koff[i];
+        cudaError_t e = kp::launch_finalize(h->P, h->S, lam + ko, R ? R + ko : nullptr, dual ? dual + i : nullptr,
+                                            primal ? primal + i : nullptr, nullptr, alpha,
+                                            lam_next ? lam_next + ko : nullptr, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t solo_select(kp_batch *b, const double *lam, double *lam_next, int round, cudaStream_t st) {
+    for (int i : b->solo) {
+        const kp_problem *h = b->probs[i];
+        const int64_t ko = b->koff[i];
+        cudaError_t e = kp::launch_select(h->P, h->S, lam + ko, lam_next + ko, round, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 kp_status kp_batch_reduce_consumption(kp_batch *b, const double *lambda, double *R, double *dual_sum,
                                       double *primal_sum, uint32_t *x_bits, void *stream) {
     if (!b || !lambda) return bfail(KP_EINVAL, "kp_batch_reduce_consumption: NULL argument");
@@ -236,7 +296,9 @@ kp_status kp_batch_reduce_consumption(kp_batch *b, const double *lambda, double 
     cudaError_t e = reset_pass(b, true, false, st);
     if (e == cudaSuccess) e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_STATE], b->G, lambda,
                                           kp::MODE_STATE, 0, x_bits, st);
+    if (e == cudaSuccess) e = solo_pass(b, lambda, kp::MODE_STATE, 0, x_bits, st);
     if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, R, dual_sum, primal_sum, 0.0, nullptr, st);
+    if (e == cudaSuccess) e = solo_finalize(b, lambda, R, dual_sum, primal_sum, 0.0, nullptr, st);
     if (e != cudaSuccess) return bfail(KP_ECUDA, "batch consumption pass", e);
     return KP_OK;
 }
@@ -250,7 +312,9 @@ kp_status kp_batch_dd_step(kp_batch *b, const double *lambda, double alpha, doub
     if (e == cudaSuccess)
         e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_STATE], b->G, lambda, kp::MODE_STATE, 0,
                                   nullptr, st);
+    if (e == cudaSuccess) e = solo_pass(b, lambda, kp::MODE_STATE, 0, nullptr, st);
     if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, nullptr, nullptr, nullptr, alpha, lambda_next, st);
+    if (e == cudaSuccess) e = solo_finalize(b, lambda, nullptr, nullptr, nullptr, alpha, lambda_next, st);
     if (e != cudaSuccess) return bfail(KP_ECUDA, "batch dual-descent step", e);
     return KP_OK;
 }
@@ -266,14 +330,19 @@ kp_status kp_batch_scd_step(kp_batch *b, const double *lambda, double *lambda_ne
     if (e == cudaSuccess)
         e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_HIST], b->G, lambda, kp::MODE_HIST, 0,
                                   nullptr, st);
+    if (e == cudaSuccess) e = solo_pass(b, lambda, kp::MODE_HIST, 0, nullptr, st);
     if (e == cudaSuccess) e = kp::launch_batch_finalize(b->B, lambda, nullptr, nullptr, nullptr, 0.0, nullptr, st);
+    if (e == cudaSuccess) e = solo_finalize(b, lambda, nullptr, nullptr, nullptr, 0.0, nullptr, st);
     if (e == cudaSuccess) e = kp::launch_batch_select(b->B, b->totK, lambda, lambda_next, 0, st);
+    if (e == cudaSuccess) e = solo_select(b, lambda, lambda_next, 0, st);
     for (int r = 1; r <= kp::MAX_REFINE && e == cudaSuccess; ++r) {
         e = reset_pass(b, false, true, st);
         if (e == cudaSuccess)
             e = kp::launch_batch_pass(b->B, b->maxm, b->smem[kp::MODE_REFINE], b->G, lambda, kp::MODE_REFINE, r,
                                   nullptr, st);
+        if (e == cudaSuccess) e = solo_pass(b, lambda, kp::MODE_REFINE, r, nullptr, st);
         if (e == cudaSuccess) e = kp::launch_batch_select(b->B, b->totK, lambda, lambda_next, r, st);
+        if (e == cudaSuccess) e = solo_select(b, lambda, lambda_next, r, st);
     }
     if (e != cudaSuccess) return bfail(KP_ECUDA, "batch SCD step", e);
     return KP_OK;

@@ -120,6 +120,7 @@ struct BatchDev {
     const int64_t *koff;    // [count + 1] offsets of each instance's multipliers
     const int64_t *xoff;    // [count] offsets of each instance's x words
     const int32_t *kinst;   // [sum K] instance of every global knapsack index
+    const uint8_t *solo;       // [count] 1: the instance runs its own passes (not in the tile list)
     const int32_t *tile_inst;  // [ntiles]
     const int64_t *tile_u0;    // [ntiles]
     unsigned long long *next;  // [MAX_REFINE + 1] tile counters, one per pass of a step

@@ -90,6 +90,7 @@ __global__ void batch_finalize_kernel(BatchDev B, const double *lam, double *R, 
     __shared__ Params sP;
     __shared__ Scratch sS;
     const int i = blockIdx.x;
+    if (B.solo[i]) return;  // finalized by its own launch
     if (threadIdx.x == 0) {
         sP = B.P[i];
         sS = B.S[i];
@@ -373,6 +374,7 @@ __global__ void batch_select_kernel(BatchDev B, const double *lam, double *lam_n
     __shared__ int s_skip;
     const int i = B.kinst[blockIdx.x];
     const int64_t ko = B.koff[i];
+    if (B.solo[i]) return;  // selected by its own launch
     if (threadIdx.x == 0) {
         sP = B.P[i];
         sS = B.S[i];

@@ -143,3 +143,55 @@ def test_batch_config_shape():
         emis = oracle.scd_map_users(p, bb, x.S, x.C, lam_h[a:b])
         check_scd_step(got[a:b], want, p, bb, lam_h[a:b], emis, floor_ulps("dense", x.K), label=f"batch inst {i}",
                        max_loose_share=1.0)
+
+
+def test_batch_with_solo_instances():
+    """A batch mixing instances that fill the GPU on their own (run by their own
+    launches inside the batched calls) with small ones (the shared persistent launch):
+    SCD steps, the consumption pass and a DD step equal the per-instance path bit for
+    bit, eagerly and replayed from a CUDA graph."""
+    from paper_2002_00352_gb300.solver import BatchScdGraph
+    big = [gen.dense_2e7(N=400_000, device="cuda"), gen.hier_m20(N=60_000, device="cuda")]
+    insts = big + _instances(count=4, seed=31, n_hi=4000)
+    batch = kp.kp_batch_create(insts)
+    probs = [kp.kp_create_from_instance(x) for x in insts]
+    lam0 = torch.zeros(batch.totK, dtype=torch.float64, device="cuda")
+    lam = lam0.clone()
+    for step in range(4):
+        nxt = torch.zeros_like(lam)
+        kp.kp_batch_scd_step(batch, lam, nxt)
+        kp.kp_batch_device_status(batch)
+        for i, (x, pr) in enumerate(zip(insts, probs)):
+            a, b = batch.koff[i], batch.koff[i + 1]
+            one = torch.zeros(x.K, dtype=torch.float64, device="cuda")
+            kp.kp_scd_step(pr, lam[a:b].contiguous(), one)
+            assert torch.equal(one, nxt[a:b]), (step, i)
+        lam = nxt
+    R = torch.zeros(batch.totK, dtype=torch.float64, device="cuda")
+    d = torch.zeros(batch.count, dtype=torch.float64, device="cuda")
+    pr_ = torch.zeros(batch.count, dtype=torch.float64, device="cuda")
+    kp.kp_batch_reduce_consumption(batch, lam, R=R, dual_sum=d, primal_sum=pr_)
+    dd = torch.zeros_like(lam)
+    kp.kp_batch_dd_step(batch, lam, 1e-3, dd)
+    kp.kp_batch_device_status(batch)
+    for i, (x, pr) in enumerate(zip(insts, probs)):
+        a, b = batch.koff[i], batch.koff[i + 1]
+        Ri = torch.zeros(x.K, dtype=torch.float64, device="cuda")
+        di = torch.zeros(1, dtype=torch.float64, device="cuda")
+        pi = torch.zeros(1, dtype=torch.float64, device="cuda")
+        kp.kp_reduce_consumption(pr, lam[a:b].contiguous(), R=Ri, dual_sum=di, primal_sum=pi)
+        assert torch.equal(Ri, R[a:b]) and torch.equal(di[0], d[i]) and torch.equal(pi[0], pr_[i]), i
+        ddi = torch.zeros(x.K, dtype=torch.float64, device="cuda")
+        kp.kp_dd_step(pr, lam[a:b].contiguous(), 1e-3, ddi)
+        assert torch.equal(ddi, dd[a:b]), i
+    g = BatchScdGraph(kp.kp_batch_create(insts), lam0)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    want = lam0.clone()
+    nb = kp.kp_batch_create(insts)
+    tmp = torch.empty_like(want)
+    for _ in range(4):
+        kp.kp_batch_scd_step(nb, want, tmp)
+        want, tmp = tmp, want
+    assert torch.equal(g.lam, want)
