@@ -28,7 +28,7 @@ def _rank(rank, world, port, values, out):
 def test_max_over_ranks_gloo_world2():
     port = _free_port()
     values = [3.25, 7.5]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(2, port, values, out), nprocs=2, join=True)
         assert out[0] == out[1] == pytest.approx(7.5)
@@ -132,7 +132,7 @@ def test_sharded_reduce_gloo_world2():
     window masses all-reduced over gloo, and the union of their in-window
     breakpoints, give exactly the single process's sums and thresholds."""
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_shard_rank, args=(2, port, out), nprocs=2, join=True)
         for r in (0, 1):
