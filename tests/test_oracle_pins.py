@@ -737,3 +737,22 @@ def test_bucketed_reduce_brackets_the_exact_reduce(seed):
             idb = int(oracle.bucket_ids(np.array([exact[k]]), lam[k], dk)[0])
             lo, hi = oracle.bucket_range(idb, lam[k], dk)
             assert abs(got - exact[k]) <= (hi - lo) * (1 + 1e-9), (seed, delta, k, got, exact[k], lo, hi)
+
+
+def test_bucket_reduce_degenerate_cases():
+    """No candidate, or all mass within the budget: 0 (Algorithm 4).  At
+    lambda^t = 0 the width is delta itself and every candidate lies above: with
+    delta = 0.25, candidates 0.1 (|d| / Delta = 0.4: bucket 0 = [-0.25, 0.25)),
+    0.3 (1.2: bucket 1 = [0.25, 0.5)) and 0.9 (3.6: bucket 2 = [0.5, 1)) of mass 1
+    each; B = 1.5: bucket 2 holds 1 <= 1.5, bucket 1 crosses:
+    0.5 - 0.5 * 0.25 = 0.375; B = 2.5: bucket 0 crosses at
+    0.25 - 0.5 * 0.5 = 0, inside its range and not below 0."""
+    assert oracle.bucket_reduce(np.array([]), np.array([]), 1.0, 0.7, 0.1) == 0.0
+    assert oracle.bucket_reduce(np.array([0.5, 0.9]), np.array([1.0, 1.0]), 2.0, 0.7, 0.1) == 0.0
+    v1 = np.array([0.1, 0.3, 0.9])
+    v2 = np.ones(3)
+    dl = oracle.bucket_delta(0.0, 0.25)
+    assert float(dl) == 0.25
+    assert oracle.bucket_ids(v1, 0.0, dl).tolist() == [0, 1, 2]
+    assert oracle.bucket_reduce(v1, v2, 1.5, 0.0, dl) == pytest.approx(0.375, abs=1e-12)
+    assert oracle.bucket_reduce(v1, v2, 2.5, 0.0, dl) == 0.0
